@@ -28,7 +28,9 @@ Readings where the paper is silent (each is listed in the design doc):
   * H is kept non-symmetric (strong zero-variance principle).
   * the diagonal shift of Sec. II.A is shift * (Gram matrix of the basis directions in parameter
     space), i.e. shift * I on the tangent space, carried into every reduced basis.
-  * "lowest" = smallest real part; a complex pair contributes its real and imaginary parts.
+  * "lowest" = smallest real part; a complex pair contributes the real and imaginary parts of its
+    eigenvector, taken with the phase that makes the largest-magnitude component real and
+    positive (only the real part when N_K ends inside the pair).
   * B^(b) rows are the beta parts of the chosen eigenvectors, each scaled to unit 2-norm with its
     largest-magnitude entry positive.
 """
@@ -154,7 +156,11 @@ def _lowest_directions(lam, vecs, k):
                        and abs(lam[j] - np.conj(li)) <= 1e-8 * max(1.0, abs(li))]
             if partner:
                 used.add(partner[0])
+            # fix the eigenvector's complex phase: largest-magnitude component real and positive,
+            # so that its real part (kept alone when N_K splits the pair) is well defined
             v = vecs[:, i]
+            kmax = np.argmax(np.abs(v))
+            v = v * (np.conj(v[kmax]) / np.abs(v[kmax]))
             out_lam.append(li.real)
             out_vec.append(v.real)
             if len(out_vec) < k:

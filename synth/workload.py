@@ -3,10 +3,13 @@
 For one optimisation (key = (seed, opt)) with n parameters this module draws, sample by sample,
   O_s = Q (sigma * z_s)                    log-derivative ratios <n|Psi^x>/<n|Psi>
   E_s = -1 + O_s . g + 0.01 * eps_s        local energy (eps normal, or Student-t with nu=3)
-  G_s = M O_s + 0.01 * eta_s               local-energy derivatives dE_L/dmu_x
-with z, eta ~ N(0, 1)^n, sigma_i = 10^(-(d/2) i/(n-1)) (so the population overlap Q diag(sigma^2) Q^T
+  G_s = M O_s + 0.01 * Q (sigma * eta_s)   local-energy derivatives dE_L/dmu_x
+with z, eta ~ N(0, 1)^n (the derivative noise has the shape of O: a parameter that barely changes
+Psi barely changes E_L), sigma_i = 10^(-(d/2) i/(n-1)) (so the population overlap Q diag(sigma^2) Q^T
 has spectrum 1 -> 10^-d), Q a product of four Householder reflectors with seeded unit vectors,
-g ~ N(0, 1/n)^n and M = Q diag(mu) Q^T with mu_i ~ U(-1/2, 1/2).  Weights are 1.
+g ~ N(0, 1/n)^n and M = Q diag(mu) Q^T with mu_i ~ U(1/2, 3/2).  Weights are 1.
+With <E> = -1 the population tangent-space energies are mu_i - 1 in [-1/2, 1/2]: the Psi direction
+lies below them, so the lowest eigenvalue of the step is real and separated, as near a VMC minimum.
 
 Every random number is a function of (seed, opt, tag, global index) through Philox4x32-10, so a
 chunk is the same whichever way the samples are split.  Nothing here computes any quantity of the
@@ -110,7 +113,7 @@ def make_model(wl: Workload) -> Model:
     i = np.arange(n, dtype=np.float64)
     sigma = 10.0 ** (-(wl.decades / 2.0) * i / max(n - 1, 1))
     g = philox.normal(wl.seed, wl.opt, TAG_G, np.arange(n, dtype=np.uint64)) / np.sqrt(n)
-    mu = philox.uniform(wl.seed, wl.opt, TAG_MU, np.arange(n, dtype=np.uint64)) - 0.5
+    mu = philox.uniform(wl.seed, wl.opt, TAG_MU, np.arange(n, dtype=np.uint64)) + 0.5
     return Model(n, u, sigma, g, mu)
 
 
@@ -148,8 +151,8 @@ def chunk(wl: Workload, model: Model, s0: int, count: int):
     z = philox.normal(wl.seed, wl.opt, TAG_Z, flat).reshape(count, n)
     O = _apply_q(model, z * model.sigma[None, :])
     eta = philox.normal(wl.seed, wl.opt, TAG_ETA, flat).reshape(count, n)
-    T = _apply_qt(model, O.copy()) * model.mu[None, :]
-    G = _apply_q(model, T) + 0.01 * eta
+    T = _apply_qt(model, O.copy()) * model.mu[None, :] + 0.01 * model.sigma[None, :] * eta
+    G = _apply_q(model, T)
     E = -1.0 + O @ model.g + 0.01 * _eps(wl, s_idx)
     if wl.offset:
         O = O + wl.offset
