@@ -1,0 +1,426 @@
+#!/usr/bin/env python
+"""Benchmark of one blocked-linear-method step on GB300 (JSON line on stdout).
+
+Workload (default): 16384 parameters in 64 blocks of 256, K = 20 kept directions per block,
+10^6 samples streamed to the library in chunks of 65536, FP32 samples resident in HBM (131 GB,
+larger than L2, so no L2 flush is needed between steps), split-BF16 tensor-core contractions
+with FP32/FP64 accumulation and FP64 centring and solves.  One step = both sweeps and both
+solves (first sweep over all chunks, block solves, second sweep over the same chunks, combined
+solve); the handle's sums are reset between steps.
+
+Metric: sample-GFLOP/s = useful FLOP of the step / step time, with the useful FLOP per sample
+3 sum_b M_b^2 (first sweep: symmetric S_b plus H_b) + 4 n K + 3 (sum_b K_b)^2 (second sweep:
+projections and combined sums).  The plain FP64 GPU path is timed on one chunk of the same
+workload (FP64 samples) and scaled to the full sample count.
+
+--impl reference times the FP64 CPU oracle (the reference implementation of the method written
+from the paper) on a bounded sample of the same workload on the host cores.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = ("n16384", "n2048", "n200")
+
+
+def useful_flop_per_sample(wl):
+    offs = wl.block_offsets
+    m = [offs[b + 1] - offs[b] for b in range(len(offs) - 1)]
+    k = [min(wl.n_keep, mb) for mb in m]
+    dc = sum(k)
+    pass1 = sum(3 * mb * mb for mb in m)
+    pass2 = 4 * wl.n * (dc / len(m)) + 3 * dc * dc
+    return pass1 + pass2
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """Samples nvidia-smi during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu=0):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+# our implementation
+# ------------------------------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import torch
+    import synth
+    from synth import device as sdev
+    import paper_1702_01481_gb300 as blm
+
+    torch.cuda.set_device(rank % max(1, torch.cuda.device_count()))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    wl = synth.workload(args.workload)
+    if args.samples:
+        wl.n_samples = args.samples
+    ns, n, chunk = wl.n_samples, wl.n, wl.chunk
+    mixed = args.precision == "bf16x4"
+    dt = torch.float32 if mixed else torch.float64
+    stream = torch.cuda.current_stream()
+
+    # inputs resident in HBM, generated on the device by the seeded generator
+    O = torch.empty((ns, n), dtype=dt, device=dev)
+    G = torch.empty((ns, n), dtype=dt, device=dev)
+    E = torch.empty((ns,), dtype=dt, device=dev)
+    dm = sdev.DeviceModel(wl, dev)
+    gen_chunk = 32768
+    for s0 in range(0, ns, gen_chunk):
+        c = min(gen_chunk, ns - s0)
+        sdev.fill(dm, s0, O[s0:s0 + c], G[s0:s0 + c], E[s0:s0 + c], stream.cuda_stream)
+    torch.cuda.synchronize()
+
+    prec = blm.BLM_PREC_BF16X4 if mixed else blm.BLM_PREC_F64
+    inp = blm.BLM_IN_F32 if mixed else blm.BLM_IN_F64
+    step = blm.Step(n, wl.block_offsets, wl.n_keep, precision=prec, input_type=inp,
+                    stream=stream.cuda_stream)
+    dmu = torch.empty(n, dtype=torch.float64, device=dev)
+
+    def one_step():
+        step.reset()
+        for s0 in range(0, ns, chunk):
+            c = min(chunk, ns - s0)
+            step.accumulate(O[s0:s0 + c], G[s0:s0 + c], E[s0:s0 + c])
+        step.block_solve()
+        for s0 in range(0, ns, chunk):
+            c = min(chunk, ns - s0)
+            step.project(O[s0:s0 + c], G[s0:s0 + c], E[s0:s0 + c])
+        return step.combined_solve(dmu)
+
+    for _ in range(args.warmup):
+        e_pred = one_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    blm.blm_profile(step.h, 1)
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for _ in range(args.steps):
+        e_pred = one_step()
+    end.record(stream)
+    torch.cuda.synchronize()
+    prof = blm.blm_profile_read(step.h)
+    blm.blm_profile(step.h, 0)
+    clk = clocks.stop()
+    elapsed_ms = start.elapsed_time(end)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        elapsed_ms = float(t.item())
+    ms_step = elapsed_ms / args.steps
+    flop = useful_flop_per_sample(wl) * ns
+    value = world * flop / (ms_step / 1e3) / 1e9
+    res = dict(wl=wl, ms_step=ms_step, value=value, prof=prof, clocks=clk, e_pred=e_pred,
+               flop=flop, steps=args.steps)
+    step.close()
+
+    # roofline of the dominant kernel
+    pk = peaks()
+    kname, (kms, klaunch) = max(prof.items(), key=lambda kv: kv[1][0])
+    res["dominant"] = kname
+    roof = None
+    if kname in ("contract_tc_pass1", "contract_f64") and klaunch:
+        per_launch_bytes = 2 * (ns / klaunch) * n * O.element_size()
+        ach = per_launch_bytes / (kms / klaunch / 1e3) / 1e9
+        p = pk.get("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": p, "unit": "GB/s",
+                "frac": round(ach / p, 4), "traffic": None,
+                "kernel": kname, "per_launch_algorithmic_bytes": per_launch_bytes,
+                "peak_source": "measured" if "hbm_gbs" in pk else "fallback"}
+    elif klaunch:
+        roof = {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": None, "kernel": kname,
+                "note": "dominant kernel is the FP64 eigen-solver (latency/FP64-ALU bound)"}
+    # tensor-core pass-1 kernel: always report its HBM roofline and executed tensor rate
+    ms1, l1 = prof.get("contract_tc_pass1", (0.0, 0))
+    if l1:
+        b1 = 2 * (ns / l1) * n * 4
+        offs = wl.block_offsets
+        m = [offs[b + 1] - offs[b] for b in range(len(offs) - 1)]
+        tiles_cols = sum(((mb + 127) // 128) * 2 * ((mb + 255) // 256) * 256 * 128 for mb in m)
+        exec_flop = 2 * 4 * tiles_cols * (ns / l1)
+        res["tc_pass1"] = {"ms_per_launch": kms and ms1 / l1, "launches": l1,
+                           "hbm_gbs": b1 / (ms1 / l1 / 1e3) / 1e9,
+                           "tensor_tflops_executed": exec_flop / (ms1 / l1 / 1e3) / 1e12,
+                           "useful_tflops": sum(3 * mb * mb for mb in m) * (ns / l1) / (ms1 / l1 / 1e3) / 1e12}
+    res["roofline"] = roof
+    res["gpu_launches"] = int(sum(v[1] for v in prof.values()))
+
+    # plain FP64 GPU path on one chunk of the same workload (FP64 samples), scaled to ns
+    if mixed and not args.no_fp64 and rank == 0:
+        del O, G, E
+        torch.cuda.empty_cache()
+        c = min(chunk, ns)
+        O64 = torch.empty((c, n), dtype=torch.float64, device=dev)
+        G64 = torch.empty((c, n), dtype=torch.float64, device=dev)
+        E64 = torch.empty((c,), dtype=torch.float64, device=dev)
+        sdev.fill(dm, 0, O64, G64, E64, stream.cuda_stream)
+        s64 = blm.Step(n, wl.block_offsets, wl.n_keep, stream=stream.cuda_stream)
+        d64 = torch.empty(n, dtype=torch.float64, device=dev)
+        blm.blm_profile(s64.h, 1)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        s64.accumulate(O64, G64, E64)
+        s64.block_solve()
+        s64.project(O64, G64, E64)
+        s64.combined_solve(d64)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        p64 = blm.blm_profile_read(s64.h)
+        total = t0.elapsed_time(t1)
+        sweeps = sum(p64[k][0] for k in ("reference_shift", "first_moments", "contract_f64",
+                                          "project"))
+        solves = total - sweeps
+        scaled = sweeps * (ns / c) + solves
+        res["fp64_path"] = {"ms_per_step_scaled": round(scaled, 1), "measured_samples": c,
+                            "measured_ms": round(total, 1), "sweep_ms": round(sweeps, 1),
+                            "solve_ms": round(solves, 1),
+                            "speedup_mixed_over_fp64": round(scaled / ms_step, 2)}
+        s64.close()
+    return res
+
+
+def run_e2e(args):
+    """Same metric through the C ABI with host (pinned) sample buffers: every step copies its
+    samples host -> device inside the timed region and reads back Delta mu and E_pred."""
+    import torch
+    import synth
+    from synth import device as sdev
+    import paper_1702_01481_gb300 as blm
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    wl = synth.workload(args.workload)
+    ns = min(wl.n_samples, args.e2e_samples)
+    n = wl.n
+    mixed = args.precision == "bf16x4"
+    dt = torch.float32 if mixed else torch.float64
+    O = torch.empty((ns, n), dtype=dt, pin_memory=True)
+    G = torch.empty((ns, n), dtype=dt, pin_memory=True)
+    E = torch.empty((ns,), dtype=dt, pin_memory=True)
+    dm = sdev.DeviceModel(wl, dev)
+    tmp = 16384
+    bo = torch.empty((tmp, n), dtype=dt, device=dev)
+    bg = torch.empty((tmp, n), dtype=dt, device=dev)
+    be = torch.empty((tmp,), dtype=dt, device=dev)
+    for s0 in range(0, ns, tmp):
+        c = min(tmp, ns - s0)
+        sdev.fill(dm, s0, bo[:c], bg[:c], be[:c])
+        O[s0:s0 + c].copy_(bo[:c])
+        G[s0:s0 + c].copy_(bg[:c])
+        E[s0:s0 + c].copy_(be[:c])
+    del bo, bg, be
+    torch.cuda.synchronize()
+    prec = blm.BLM_PREC_BF16X4 if mixed else blm.BLM_PREC_F64
+    inp = blm.BLM_IN_F32 if mixed else blm.BLM_IN_F64
+    stream = torch.cuda.current_stream()
+    step = blm.Step(n, wl.block_offsets, wl.n_keep, precision=prec, input_type=inp,
+                    stream=stream.cuda_stream)
+    dmu = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    chunk = wl.chunk
+
+    def one_step():
+        step.reset()
+        for s0 in range(0, ns, chunk):
+            c = min(chunk, ns - s0)
+            step.accumulate(O[s0:s0 + c], G[s0:s0 + c], E[s0:s0 + c])
+        step.block_solve()
+        for s0 in range(0, ns, chunk):
+            c = min(chunk, ns - s0)
+            step.project(O[s0:s0 + c], G[s0:s0 + c], E[s0:s0 + c])
+        return step.combined_solve(dmu)
+
+    one_step()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    steps = max(1, args.e2e_steps)
+    for _ in range(steps):
+        one_step()
+    torch.cuda.synchronize()
+    sec = (time.perf_counter() - t) / steps
+    step.close()
+    flop = useful_flop_per_sample(wl) * ns
+    h2d = 2 * 2 * ns * n * O.element_size() + 2 * ns * E.element_size()
+    return {"value": round(flop / sec / 1e9, 1), "unit": "sample-GFLOP/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 * n + 8,
+            "samples_per_step": ns, "ms_per_step": round(sec * 1e3, 1)}
+
+
+def cpu_baseline(args, wl, samples):
+    """The FP64 oracle on the host cores on a bounded sample of the same workload."""
+    import numpy as np
+    import synth
+    from oracle import blm_oracle
+    O, G, E = synth.samples(wl, count=samples, dtype=np.float32)
+    O, G, E = (a.astype(np.float64) for a in (O, G, E))
+    t = time.perf_counter()
+    blm_oracle.blm_step(O, G, E, None, wl.block_offsets, wl.n_keep)
+    sec = time.perf_counter() - t
+    flop = useful_flop_per_sample(wl) * samples
+    return {"value": round(flop / sec / 1e9, 3), "unit": "sample-GFLOP/s",
+            "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "%d of %d samples of the same workload (full parameter count), one step, %.1f s"
+                      % (samples, wl.n_samples, sec)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="n16384", choices=WORKLOADS)
+    ap.add_argument("--precision", default=None, choices=["bf16x4", "f64"])
+    ap.add_argument("--samples", type=int, default=0)
+    ap.add_argument("--cpu-samples", type=int, default=2048)
+    ap.add_argument("--e2e-samples", type=int, default=131072)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.precision is None:
+        args.precision = "bf16x4" if args.workload == "n16384" else "f64"
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    import synth
+    wl = synth.workload(args.workload)
+    if args.samples:
+        wl.n_samples = args.samples
+    config = {"workload": "%s: n=%d params, N_B=%d blocks, K=%d, N_s=%d samples in chunks of %d, %s"
+                          % (args.workload, wl.n, wl.n_blocks, wl.n_keep, wl.n_samples, wl.chunk,
+                             "split-BF16 tensor-core sweeps + FP64 solves" if args.precision == "bf16x4"
+                             else "FP64 sweeps + FP64 solves"),
+              "input": "FP32 samples resident in HBM" if args.precision == "bf16x4" else "FP64 samples resident in HBM",
+              "l2": "inputs larger than L2 (no flush needed)",
+              "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
+    metric = "blocked-LM step: sample-GFLOP/s (useful FLOP of both sweeps / step time)"
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps = []
+        samples = max(64, args.cpu_samples // 2)
+        for _ in range(args.warmup):
+            cpu_baseline(args, wl, 64)
+        for _ in range(args.steps):
+            steps.append(cpu_baseline(args, wl, samples))
+        v = sorted(s["value"] for s in steps)[len(steps) // 2]
+        flop = useful_flop_per_sample(wl) * wl.n_samples
+        line = {"impl": "reference", "metric": metric, "value": v, "unit": "sample-GFLOP/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(flop / (v * 1e9) * 1e3, 1),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded generator)", "config": config,
+                "cpu_baseline": {"value": v, "unit": "sample-GFLOP/s", "cores": os.cpu_count(),
+                                 "kind": "oracle", "sample": steps[0]["sample"]},
+                "e2e": {"value": v, "unit": "sample-GFLOP/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    res = run_ours(args, rank, world)
+    if rank != 0:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+        return
+    line = {"metric": metric, "value": round(res["value"], 1), "unit": "sample-GFLOP/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(res["ms_step"], 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x4/f32-acc/f64-solve" if args.precision == "bf16x4" else "f64",
+            "data": "synthetic (seeded generator, on device)", "config": config,
+            "e_pred": res["e_pred"], "roofline": res["roofline"], "clocks": res["clocks"],
+            "gpu_launches": res["gpu_launches"],
+            "phases_ms_per_step": {k: round(v[0] / res["steps"], 2) for k, v in res["prof"].items() if v[1]},
+            "dominant_kernel": res["dominant"]}
+    if "tc_pass1" in res:
+        line["tc_pass1"] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in res["tc_pass1"].items()}
+    if "fp64_path" in res:
+        line["fp64_path"] = res["fp64_path"]
+    if not args.no_e2e and world == 1:
+        line["e2e"] = run_e2e(args)
+    else:
+        line["e2e"] = None
+    if not args.no_cpu and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args, wl, args.cpu_samples)
+    print(json.dumps(line))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

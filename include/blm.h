@@ -1,0 +1,162 @@
+/*
+ * blm.h -- C ABI of the GB300 library for one step of the blocked linear method (BLM) of
+ * Zhao & Neuscamman, "A Blocked Linear Method for Optimizing Large Parameter Sets in
+ * Variational Monte Carlo" (arXiv:1702.01481).
+ *
+ * One step, in call order (Sec. II.B):
+ *   blm_accumulate      per sample chunk: Monte Carlo sums of Eq. 3 for every block's
+ *                       self-plus-tangent space (Eq. 5; with history directions, Eq. 9-10)
+ *   blm_block_solve     per block: generalized eigenproblem, keep the N_K lowest directions
+ *                       as the rows of B^(b)
+ *   blm_project         per sample chunk, the SAME samples again ("re-run the same sample"):
+ *                       project onto the retained directions and accumulate Eq. 7's sums
+ *   blm_combined_solve  lowest eigenpair of Eq. 7, update of Eq. 8, predicted energy
+ *
+ * Inputs per sample s (row s of each array, parameters contiguous, row stride `ld` elements):
+ *   O[s, x]   = <n_s|Psi^x>/<n_s|Psi>          log-derivative ratio of parameter x
+ *   dEL[s, x] = d E_L(n_s) / d mu_x            derivative of the local energy
+ *   EL[s]     = <n_s|H|Psi>/<n_s|Psi>          local energy
+ *   w[s]      = |<n_s|Psi>|^2 / P(n_s)         weight (NULL means 1, i.e. P = |Psi|^2)
+ * The Hamiltonian ratio of Eq. 3 is <n|H|Psi^x>/<n|Psi> = EL * O_x + dEL_x.
+ *
+ * Conventions
+ *   - Sample arrays may be device memory or host memory (pinned or pageable); host arrays are
+ *     copied through the handle's staging buffers.  Element type per blm_problem.input_type.
+ *   - All calls are asynchronous on the handle's stream; results are valid once it syncs.
+ *   - The handle owns every accumulator and workspace it needs (allocated in blm_create).
+ *   - Call order is enforced: accumulate+ -> block_solve -> project+ -> combined_solve;
+ *     a call out of order returns BLM_ERR_STATE and changes nothing.
+ *   - Numeric failures (non-finite sums, overlap not positive definite, no real lowest
+ *     eigenvalue, alpha ~ 0) return BLM_ERR_NUMERIC from the solve that meets them;
+ *     blm_last_error() gives a one-line reason.
+ *   - Device waits inside the library are bounded: a wait that runs out returns
+ *     BLM_ERR_TIMEOUT instead of hanging.
+ */
+#ifndef BLM_H
+#define BLM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BLM_OK = 0,
+  BLM_ERR_ARG = 1,          /* invalid argument (sizes, pointers, offsets)               */
+  BLM_ERR_STATE = 2,        /* call out of order                                          */
+  BLM_ERR_NUMERIC = 3,      /* see blm_last_error()                                       */
+  BLM_ERR_NOMEM = 4,        /* device allocation failed                                   */
+  BLM_ERR_CUDA = 5,         /* a CUDA call failed (message in blm_last_error())           */
+  BLM_ERR_TIMEOUT = 6,      /* a bounded device wait ran out                              */
+  BLM_ERR_UNSUPPORTED = 7   /* valid but not implemented combination                      */
+} blm_status;
+
+typedef enum {
+  BLM_PREC_F64 = 0,    /* sample contractions in FP64 on CUDA cores                         */
+  BLM_PREC_BF16X4 = 1  /* sample contractions on tcgen05 tensor cores: each operand split into
+                          bf16 hi + lo, four products accumulated in FP32 (TMEM), promoted to
+                          FP64; centring corrections and eigen-solves stay FP64               */
+} blm_precision;
+
+typedef enum { BLM_IN_F64 = 0, BLM_IN_F32 = 1 } blm_input_type;
+
+typedef struct {
+  int64_t n_params;               /* N_V                                                     */
+  int32_t n_blocks;               /* N_B                                                     */
+  const int64_t* block_offsets;   /* host, n_blocks+1 increasing, [0] = 0, [N_B] = N_V;
+                                     block b is parameters [off[b], off[b+1]) (contiguous)   */
+  int32_t n_keep;                 /* N_K: directions kept per block (min(N_K, M_b) used)     */
+  int32_t n_old;                  /* N_O: previous-update directions (Eq. 9), 0 = none       */
+  const double* old_dirs;         /* host or device, n_old x n_params row-major: row j is the
+                                     overall update of iteration n-j (Sec. II.B); block k's
+                                     slice of row j is D_jk.  Copied at blm_create.          */
+  int32_t precision;              /* blm_precision                                           */
+  int32_t input_type;             /* blm_input_type                                          */
+  double shift;                   /* diagonal shift of Sec. II.A on the tangent space (>= 0) */
+} blm_problem;
+
+typedef struct blm_handle blm_handle;
+
+/* Sec. II.B.  Validates the problem, allocates the handle's device memory on the current
+ * device and binds the handle to `stream` (a cudaStream_t; NULL = legacy default stream).
+ * Returns BLM_ERR_ARG for invalid sizes/offsets, BLM_ERR_NOMEM if allocation fails.
+ * On failure *out is NULL. */
+blm_status blm_create(const blm_problem* problem, void* stream, blm_handle** out);
+
+/* Sec. II.A Eq. 3 and Sec. II.B Eq. 5/10, first sweep.  Adds one chunk of n_samples samples
+ * to every block's sums.  O and dEL are n_samples x ld (ld >= n_params), EL and w length
+ * n_samples, all of the problem's input type; w may be NULL.  The first call also fixes the
+ * per-parameter reference shift used for centring (the chunk's mean of O).  n_samples == 0 is
+ * a no-op.  Chunks may have any sizes. */
+blm_status blm_accumulate(blm_handle* h, const void* O, const void* dEL, const void* EL,
+                          const void* w, int64_t n_samples, int64_t ld);
+
+/* Sec. II.B Eq. 5 / Eq. 10.  Builds every block's overlap and Hamiltonian from the sums (mean
+ * centring in FP64), solves each generalized eigenproblem and keeps the min(N_K, M_b) lowest
+ * directions (smallest real part; a complex pair gives its real and imaginary parts) as the
+ * rows of B^(b), each of unit 2-norm with its largest-magnitude entry positive.
+ * BLM_ERR_STATE before any accumulate; BLM_ERR_NUMERIC if a block's overlap is not positive
+ * definite or its sums are not finite. */
+blm_status blm_block_solve(blm_handle* h);
+
+/* Sec. II.B, second sweep over the same samples (Eq. 6-7 matrices).  Same argument rules as
+ * blm_accumulate.  The chunks must be the ones given to blm_accumulate (any order). */
+blm_status blm_project(blm_handle* h, const void* O, const void* dEL, const void* EL,
+                       const void* w, int64_t n_samples, int64_t ld);
+
+/* Sec. II.B Eq. 7-8.  Solves the combined problem of dimension 1 + sum_b min(N_K, M_b), takes
+ * its lowest eigenpair (c_0, A) and writes Delta mu_{i,b} = sum_j A_bj B^(b)_ji / alpha into
+ * dmu (device or host, n_params doubles) and the eigenvalue (the predicted energy) into
+ * *e_pred (host).  alpha is the coefficient of the raw Psi, c_0 - sum_bj A_bj (B^(b)_j . <O_b>).
+ * Synchronises the handle's stream.  BLM_ERR_NUMERIC if the lowest eigenvalue is complex or
+ * alpha ~ 0. */
+blm_status blm_combined_solve(blm_handle* h, double* dmu, double* e_pred);
+
+/* Read back block b's matrices (host, row-major (1+d_b)^2 with d_b = M_b + N_O (N_B - 1)),
+ * its kept eigenvalues (host, min(N_K,M_b)) and B^(b) (host, min(N_K,M_b) x M_b).  Any output
+ * pointer may be NULL.  Valid after blm_block_solve; synchronises the stream. */
+blm_status blm_get_block(blm_handle* h, int32_t b, double* S, double* H, double* lambda,
+                         double* B);
+
+/* Combined matrices (host, row-major (1+N_K_total)^2), valid after blm_combined_solve. */
+blm_status blm_get_combined(blm_handle* h, double* S, double* H);
+
+/* Dimensions: block b's tangent dimension d_b, and the combined tangent dimension. */
+int64_t blm_block_dim(const blm_handle* h, int32_t b);
+int64_t blm_combined_dim(const blm_handle* h);
+
+/* Clears all sums and solutions so that a new step can start with the same problem. */
+blm_status blm_reset(blm_handle* h);
+
+/* Frees the handle (NULL is a no-op). */
+blm_status blm_destroy(blm_handle* h);
+
+/* Last error message of the handle ("" if none); valid until the next call on it. */
+const char* blm_last_error(const blm_handle* h);
+
+/* Profiling (no counterpart in the paper: measurement support).  While enabled, the handle
+ * records a pair of CUDA events on its stream around each kernel it launches and counts the
+ * launches, per kernel class.  blm_profile_read synchronises the stream and fills, for classes
+ * 0 .. n-1 (n <= BLM_PROF_CLASSES), the summed device milliseconds and launch counts since the
+ * last reset (enable != 0 also resets).  blm_profile_class_name(i) names class i. */
+#define BLM_PROF_CLASSES 12
+blm_status blm_profile(blm_handle* h, int enable);
+blm_status blm_profile_read(blm_handle* h, int n, double* ms, int64_t* launches);
+const char* blm_profile_class_name(int i);
+
+/* Device bytes blm_create allocates for this problem (0 if the problem is invalid).  Host
+ * function: needs no GPU. */
+size_t blm_memory_estimate(const blm_problem* problem);
+
+/* Storage of Sec. II.B's memory discussion, in bytes of 8-byte words: the traditional LM's
+ * H and S, 2 (1 + N_V)^2, and the BLM's dominant terms (N_V^2/N_B + 2 N_V N_O (N_B - 1)
+ * for H, N_V^2/N_B + N_V N_O (N_B - 1) for the symmetric S).  Host functions. */
+double blm_lm_matrix_bytes(int64_t n_params);
+double blm_matrix_bytes_dominant(int64_t n_params, int32_t n_blocks, int32_t n_old);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BLM_H */

@@ -1,0 +1,722 @@
+// FP64 generalized eigen-solver for the block problems (Eq. 5 / Eq. 10) and the combined problem
+// (Eq. 7) of the blocked linear method: H v = lambda S v with H non-symmetric and S symmetric
+// positive definite, keeping the eigenpairs with the lowest real parts (Sec. II.B).
+//
+// One CTA per problem (all blocks in one launch).  Steps, all FP64:
+//   1. diagonal scaling  S~ = D S D, H~ = D H D with D = diag(S)^-1/2;
+//   2. Cholesky  S~ = L L^T  and reduction to standard form  A = L^-1 H~ L^-T;
+//   3. Householder reduction of A to upper Hessenberg form  A = Q Hs Q^T;
+//   4. Francis double-shift QR on Hs for all eigenvalues (eigenvalues only, active window);
+//   5. for each wanted eigenvalue, inverse iteration on the Hessenberg matrix (real or complex
+//      LU with the one-row partial pivoting a Hessenberg matrix needs);
+//   6. back-transformation  v = D L^-T Q y.
+// Iterations are bounded: a QR that does not converge within 40 m sweeps reports ST_NOCONV.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "blm_internal.cuh"
+
+namespace blm {
+
+namespace {
+
+constexpr int kEigThreads = 512;
+constexpr int kMaxKeep = 64;
+
+struct cplx {
+  double re, im;
+};
+__device__ __forceinline__ cplx cmk(double r, double i) { return cplx{r, i}; }
+__device__ __forceinline__ cplx operator-(cplx a, cplx b) { return cmk(a.re - b.re, a.im - b.im); }
+__device__ __forceinline__ cplx operator*(cplx a, cplx b) {
+  return cmk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+__device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
+  // Smith's algorithm
+  if (fabs(b.re) >= fabs(b.im)) {
+    const double r = b.im / b.re, d = b.re + b.im * r;
+    return cmk((a.re + a.im * r) / d, (a.im - a.re * r) / d);
+  }
+  const double r = b.re / b.im, d = b.re * r + b.im;
+  return cmk((a.re * r + a.im) / d, (a.im * r - a.re) / d);
+}
+__device__ __forceinline__ double cabs2(cplx a) { return fabs(a.re) + fabs(a.im); }
+
+// Banded upper-Hessenberg store used by the QR sweeps: row i keeps columns [max(0, i-3), m),
+// room for the Hessenberg part plus the 3 x 3 bulge of a double-shift step.
+struct Band {
+  double* p;
+  int m;
+  __device__ __forceinline__ int64_t off(int i) const {
+    if (i <= 4) return (int64_t)i * m;
+    const int64_t r = i - 4;
+    return 4LL * m + r * (m + 3) - (((int64_t)(i - 1) * i) / 2 - 6);
+  }
+  __device__ __forceinline__ double& at(int i, int j) const {
+    const int c0 = i > 3 ? i - 3 : 0;
+    return p[off(i) + (j - c0)];
+  }
+  __host__ __device__ static int64_t size(int m) {
+    if (m <= 4) return (int64_t)m * m;
+    const int64_t i = m, r = i - 4;
+    return 4LL * m + r * (m + 3) - ((i - 1) * i / 2 - 6);
+  }
+};
+
+__device__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  const int nw = blockDim.x >> 5;
+  for (int i = 0; i < nw; ++i) s += red[i];
+  return s;
+}
+
+__device__ double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  const int nw = blockDim.x >> 5;
+  for (int i = 0; i < nw; ++i) s = fmax(s, red[i]);
+  return s;
+}
+
+// 3-vector (or 2-vector) Householder: returns beta, v = (1, v1, v2) with
+// (I - beta v v^T) (x, y, z)^T = (alpha, 0, 0)^T.
+__device__ void house3(double x, double y, double z, double& beta, double& v1, double& v2) {
+  const double sigma = y * y + z * z;
+  if (sigma == 0.0) {
+    beta = 0.0;
+    v1 = v2 = 0.0;
+    return;
+  }
+  const double mu = sqrt(x * x + sigma);
+  const double v0 = (x <= 0.0) ? (x - mu) : (-sigma / (x + mu));
+  beta = 2.0 * v0 * v0 / (sigma + v0 * v0);
+  v1 = y / v0;
+  v2 = z / v0;
+}
+
+struct Shared {
+  double red[32];
+  double scal[8];
+  int iscal[8];
+  int sel_idx[kMaxKeep];
+  int sel_part[kMaxKeep];   // 0 real, 1 real part of complex, 2 imaginary part of complex
+};
+
+// ---------------------------------------------------------------------------------------------
+// QR iteration for all eigenvalues of the Hessenberg matrix in `h` (banded store).
+// Returns false if it did not converge.
+// ---------------------------------------------------------------------------------------------
+__device__ bool hqr_eigenvalues(Band h, int m, double* wr, double* wi, double anorm, Shared& sh) {
+  const int t = threadIdx.x, nt = blockDim.x;
+  const double eps = 2.220446049250313e-16;
+  int hi = m - 1;
+  int its = 0, total = 0;
+  const int limit = 40 * m + 100;
+  while (hi >= 0) {
+    // --- deflation search (thread 0), broadcast l ---
+    if (t == 0) {
+      int l = hi;
+      while (l > 0) {
+        double s = fabs(h.at(l - 1, l - 1)) + fabs(h.at(l, l));
+        if (s == 0.0) s = anorm;
+        if (fabs(h.at(l, l - 1)) <= eps * s) {
+          h.at(l, l - 1) = 0.0;
+          break;
+        }
+        --l;
+      }
+      sh.iscal[0] = l;
+    }
+    __syncthreads();
+    const int l = sh.iscal[0];
+    __syncthreads();
+    if (l == hi) {
+      if (t == 0) {
+        wr[hi] = h.at(hi, hi);
+        wi[hi] = 0.0;
+      }
+      hi -= 1;
+      its = 0;
+      __syncthreads();
+      continue;
+    }
+    if (l == hi - 1) {
+      if (t == 0) {
+        const double a = h.at(hi - 1, hi - 1), b = h.at(hi - 1, hi);
+        const double c = h.at(hi, hi - 1), d = h.at(hi, hi);
+        const double p = 0.5 * (a - d);
+        const double disc = p * p + b * c;
+        const double mid = 0.5 * (a + d);
+        if (disc >= 0.0) {
+          const double s = sqrt(disc);
+          const double l1 = mid + (mid >= 0.0 ? s : -s);
+          double l2 = mid - (mid >= 0.0 ? s : -s);
+          const double det = a * d - b * c;
+          if (l1 != 0.0) l2 = det / l1;
+          wr[hi - 1] = fmin(l1, l2);
+          wr[hi] = fmax(l1, l2);
+          wi[hi - 1] = wi[hi] = 0.0;
+        } else {
+          const double s = sqrt(-disc);
+          wr[hi - 1] = wr[hi] = mid;
+          wi[hi - 1] = s;
+          wi[hi] = -s;
+        }
+      }
+      hi -= 2;
+      its = 0;
+      __syncthreads();
+      continue;
+    }
+    if (total >= limit) return false;
+    ++its;
+    ++total;
+    // --- shifts and first column (thread 0) ---
+    if (t == 0) {
+      double s, tt;
+      if (its % 11 == 10) {
+        const double e = fabs(h.at(hi, hi - 1)) + fabs(h.at(hi - 1, hi - 2));
+        s = 1.5 * e;
+        tt = e * e;
+      } else {
+        s = h.at(hi - 1, hi - 1) + h.at(hi, hi);
+        tt = h.at(hi - 1, hi - 1) * h.at(hi, hi) - h.at(hi - 1, hi) * h.at(hi, hi - 1);
+      }
+      const double h00 = h.at(l, l), h10 = h.at(l + 1, l), h01 = h.at(l, l + 1);
+      const double h11 = h.at(l + 1, l + 1), h21 = h.at(l + 2, l + 1);
+      sh.scal[0] = h00 * h00 + h01 * h10 - s * h00 + tt;
+      sh.scal[1] = h10 * (h00 + h11 - s);
+      sh.scal[2] = h10 * h21;
+    }
+    __syncthreads();
+    double x = sh.scal[0], y = sh.scal[1], z = sh.scal[2];
+    __syncthreads();
+    for (int k = l; k <= hi - 1; ++k) {
+      const bool three = (k <= hi - 2);
+      if (t == 0) {
+        double beta, v1, v2;
+        house3(x, y, three ? z : 0.0, beta, v1, v2);
+        sh.scal[3] = beta;
+        sh.scal[4] = v1;
+        sh.scal[5] = three ? v2 : 0.0;
+      }
+      __syncthreads();
+      const double beta = sh.scal[3], v1 = sh.scal[4], v2 = sh.scal[5];
+      if (beta != 0.0) {
+        const int c0 = (k > l) ? k - 1 : l;
+        for (int j = c0 + t; j <= hi; j += nt) {
+          if (three) {
+            double p = h.at(k, j) + v1 * h.at(k + 1, j) + v2 * h.at(k + 2, j);
+            p *= beta;
+            h.at(k, j) -= p;
+            h.at(k + 1, j) -= p * v1;
+            h.at(k + 2, j) -= p * v2;
+          } else {
+            double p = h.at(k, j) + v1 * h.at(k + 1, j);
+            p *= beta;
+            h.at(k, j) -= p;
+            h.at(k + 1, j) -= p * v1;
+          }
+        }
+        __syncthreads();
+        if (t == 0 && k > l) {
+          h.at(k + 1, k - 1) = 0.0;
+          if (three) h.at(k + 2, k - 1) = 0.0;
+        }
+        const int rmax = three ? min(k + 3, hi) : hi;
+        for (int i = l + t; i <= rmax; i += nt) {
+          if (three) {
+            double p = h.at(i, k) + v1 * h.at(i, k + 1) + v2 * h.at(i, k + 2);
+            p *= beta;
+            h.at(i, k) -= p;
+            h.at(i, k + 1) -= p * v1;
+            h.at(i, k + 2) -= p * v2;
+          } else {
+            double p = h.at(i, k) + v1 * h.at(i, k + 1);
+            p *= beta;
+            h.at(i, k) -= p;
+            h.at(i, k + 1) -= p * v1;
+          }
+        }
+      }
+      __syncthreads();
+      if (k < hi - 1) {
+        x = h.at(k + 1, k);
+        y = h.at(k + 2, k);
+        z = (k < hi - 2) ? h.at(k + 3, k) : 0.0;
+      }
+      __syncthreads();
+    }
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Inverse iteration on the Hessenberg matrix Hh (row-major m x m) for eigenvalue lam (complex
+// allowed).  Writes the eigenvector (re, im) into yr, yi.  W: 2 m^2 doubles of workspace.
+// ---------------------------------------------------------------------------------------------
+__device__ void hess_inverse_iteration(const double* Hh, int m, double lre, double lim,
+                                       double anorm, double* W, double* yr, double* yi,
+                                       double* piv_l_re, double* piv_l_im, int* piv_swap,
+                                       Shared& sh) {
+  const int t = threadIdx.x, nt = blockDim.x;
+  const bool cx = (lim != 0.0);
+  double* Ur = W;
+  double* Ui = W + (int64_t)m * m;
+  // perturb the shift slightly so that the LU is not exactly singular
+  const double pert = anorm * 1e-14;
+  const double sre = lre + pert;
+  const double sim = lim;
+  for (int64_t idx = t; idx < (int64_t)m * m; idx += nt) {
+    const int i = (int)(idx / m), j = (int)(idx % m);
+    double v = (j >= i - 1) ? Hh[idx] : 0.0;
+    if (i == j) v -= sre;
+    Ur[idx] = v;
+    if (cx) Ui[idx] = (i == j) ? -sim : 0.0;
+  }
+  __syncthreads();
+  // LU with partial pivoting between rows k and k+1
+  for (int k = 0; k < m - 1; ++k) {
+    if (t == 0) {
+      cplx a = cmk(Ur[(int64_t)k * m + k], cx ? Ui[(int64_t)k * m + k] : 0.0);
+      cplx b = cmk(Ur[(int64_t)(k + 1) * m + k], cx ? Ui[(int64_t)(k + 1) * m + k] : 0.0);
+      int sw = cabs2(b) > cabs2(a) ? 1 : 0;
+      if (sw) {
+        const cplx tmp = a;
+        a = b;
+        b = tmp;
+      }
+      if (cabs2(a) == 0.0) a = cmk(pert, 0.0);
+      const cplx l = cdiv(b, a);
+      piv_swap[k] = sw;
+      piv_l_re[k] = l.re;
+      piv_l_im[k] = l.im;
+    }
+    __syncthreads();
+    const int sw = piv_swap[k];
+    const cplx l = cmk(piv_l_re[k], piv_l_im[k]);
+    for (int j = k + t; j < m; j += nt) {
+      const int64_t ik = (int64_t)k * m + j, ik1 = (int64_t)(k + 1) * m + j;
+      cplx a = cmk(Ur[ik], cx ? Ui[ik] : 0.0);
+      cplx b = cmk(Ur[ik1], cx ? Ui[ik1] : 0.0);
+      if (sw) {
+        const cplx tmp = a;
+        a = b;
+        b = tmp;
+      }
+      b = b - l * a;
+      Ur[ik] = a.re;
+      Ur[ik1] = b.re;
+      if (cx) {
+        Ui[ik] = a.im;
+        Ui[ik1] = b.im;
+      }
+    }
+    __syncthreads();
+  }
+  // right-hand side: start from a fixed vector; iterate solves
+  for (int i = t; i < m; i += nt) {
+    yr[i] = 1.0 + 0.1 * (double)((i * 7919) % 97) / 97.0;
+    yi[i] = 0.0;
+  }
+  __syncthreads();
+  for (int iter = 0; iter < 3; ++iter) {
+    // forward: apply the row swaps and multipliers
+    if (t == 0) {
+      for (int k = 0; k < m - 1; ++k) {
+        cplx a = cmk(yr[k], yi[k]), b = cmk(yr[k + 1], yi[k + 1]);
+        if (piv_swap[k]) {
+          const cplx tmp = a;
+          a = b;
+          b = tmp;
+        }
+        b = b - cmk(piv_l_re[k], piv_l_im[k]) * a;
+        yr[k] = a.re;
+        yi[k] = a.im;
+        yr[k + 1] = b.re;
+        yi[k + 1] = b.im;
+      }
+    }
+    __syncthreads();
+    // back substitution with U (column oriented)
+    for (int k = m - 1; k >= 0; --k) {
+      if (t == 0) {
+        cplx d = cmk(Ur[(int64_t)k * m + k], cx ? Ui[(int64_t)k * m + k] : 0.0);
+        if (cabs2(d) == 0.0) d = cmk(pert, 0.0);
+        const cplx xk = cdiv(cmk(yr[k], yi[k]), d);
+        yr[k] = xk.re;
+        yi[k] = xk.im;
+      }
+      __syncthreads();
+      const cplx xk = cmk(yr[k], yi[k]);
+      for (int i = t; i < k; i += nt) {
+        const cplx u = cmk(Ur[(int64_t)i * m + k], cx ? Ui[(int64_t)i * m + k] : 0.0);
+        const cplx v = cmk(yr[i], yi[i]) - u * xk;
+        yr[i] = v.re;
+        yi[i] = v.im;
+      }
+      __syncthreads();
+    }
+    // normalise (max-abs)
+    double mx = 0.0;
+    for (int i = t; i < m; i += nt) mx = fmax(mx, fabs(yr[i]) + fabs(yi[i]));
+    mx = block_max(mx, sh.red);
+    const double inv = mx > 0.0 ? 1.0 / mx : 1.0;
+    for (int i = t; i < m; i += nt) {
+      yr[i] *= inv;
+      yi[i] *= inv;
+    }
+    __syncthreads();
+  }
+}
+
+// v <- D L^-T Q v  for a real vector v (Q from the stored Householder vectors in A).
+__device__ void back_transform(const double* A, const double* hbeta, const double* L,
+                               const double* dsc, int m, double* v, Shared& sh) {
+  const int t = threadIdx.x, nt = blockDim.x;
+  // Q = P_0 P_1 ... P_{m-3}; apply P_{m-3} first.  P_k acts on indices k+1..m-1 with
+  // u = (1, A[k+2][k], ..., A[m-1][k]).
+  for (int k = m - 3; k >= 0; --k) {
+    const double beta = hbeta[k];
+    if (beta == 0.0) continue;
+    double part = 0.0;
+    for (int i = k + 1 + t; i < m; i += nt) {
+      const double u = (i == k + 1) ? 1.0 : A[(int64_t)i * m + k];
+      part += u * v[i];
+    }
+    const double dot = block_sum(part, sh.red);
+    for (int i = k + 1 + t; i < m; i += nt) {
+      const double u = (i == k + 1) ? 1.0 : A[(int64_t)i * m + k];
+      v[i] -= beta * dot * u;
+    }
+    __syncthreads();
+  }
+  // z = L^-T v  (L lower, row-major): for i = m-1..0: z_i = v_i / L_ii; v_j -= L_ij z_i (j < i)
+  for (int i = m - 1; i >= 0; --i) {
+    if (t == 0) v[i] = v[i] / L[(int64_t)i * m + i];
+    __syncthreads();
+    const double zi = v[i];
+    for (int j = t; j < i; j += nt) v[j] -= L[(int64_t)i * m + j] * zi;
+    __syncthreads();
+  }
+  for (int i = t; i < m; i += nt) v[i] *= dsc[i];
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kEigThreads)
+eig_kernel(const EigProblem* __restrict__ probs) {
+  extern __shared__ double dsm[];
+  __shared__ Shared sh;
+  const EigProblem pb = probs[blockIdx.x];
+  const int m = pb.m;
+  const int t = threadIdx.x, nt = blockDim.x;
+  const int64_t mm = (int64_t)m * m;
+  double* L = pb.work;
+  double* A = L + mm;
+  double* Hh = A + mm;
+  double* W = Hh + mm;            // 2 m^2 (band store for QR, then LU workspace)
+  double* dsc = W + 2 * mm;
+  double* hbeta = dsc + m;
+  double* wr = hbeta + m;
+  double* wi = wr + m;
+  double* yr = wi + m;
+  double* yi = yr + m;
+  double* col = yi + m;           // m
+  double* plr = col + m;
+  double* pli = plr + m;
+  int* pswap = reinterpret_cast<int*>(pli + m);
+  double* vtmp = pli + 2 * m;     // m
+
+  if (t == 0) sh.iscal[1] = ST_OK;
+  __syncthreads();
+  // ---- 1. scaling ----
+  for (int i = t; i < m; i += nt) {
+    const double s = pb.S[(int64_t)i * m + i];
+    if (!(s > 0.0) || !isfinite(s)) sh.iscal[1] = ST_NOT_PD;
+    dsc[i] = (s > 0.0) ? 1.0 / sqrt(s) : 0.0;
+  }
+  __syncthreads();
+  if (sh.iscal[1] != ST_OK) {
+    if (t == 0) *pb.status = sh.iscal[1];
+    return;
+  }
+  for (int64_t idx = t; idx < mm; idx += nt) {
+    const int i = (int)(idx / m), j = (int)(idx % m);
+    const double sv = pb.S[idx] * dsc[i] * dsc[j];
+    const double hv = pb.H[idx] * dsc[i] * dsc[j];
+    if (!isfinite(sv) || !isfinite(hv)) sh.iscal[1] = ST_NONFINITE;
+    L[idx] = sv;
+    A[idx] = hv;
+  }
+  __syncthreads();
+  if (sh.iscal[1] != ST_OK) {
+    if (t == 0) *pb.status = sh.iscal[1];
+    return;
+  }
+  // ---- 2a. Cholesky (right-looking, lower) ----
+  for (int k = 0; k < m; ++k) {
+    if (t == 0) {
+      const double p = L[(int64_t)k * m + k];
+      if (!(p > 1e-15)) {
+        sh.iscal[1] = ST_NOT_PD;
+      } else {
+        L[(int64_t)k * m + k] = sqrt(p);
+        sh.scal[0] = 1.0 / sqrt(p);
+      }
+    }
+    __syncthreads();
+    if (sh.iscal[1] != ST_OK) break;
+    const double inv = sh.scal[0];
+    for (int i = k + 1 + t; i < m; i += nt) {
+      const double v = L[(int64_t)i * m + k] * inv;
+      L[(int64_t)i * m + k] = v;
+      col[i] = v;
+    }
+    __syncthreads();
+    const int r = m - k - 1;
+    for (int64_t idx = t; idx < (int64_t)r * r; idx += nt) {
+      const int ii = (int)(idx / r), jj = (int)(idx % r);
+      if (jj <= ii) {
+        const int i = k + 1 + ii, j = k + 1 + jj;
+        L[(int64_t)i * m + j] -= col[i] * col[j];
+      }
+    }
+    __syncthreads();
+  }
+  if (sh.iscal[1] != ST_OK) {
+    if (t == 0) *pb.status = sh.iscal[1];
+    return;
+  }
+  // ---- 2b. A <- L^-1 A (row forward substitution) ----
+  for (int k = 0; k < m; ++k) {
+    const double inv = 1.0 / L[(int64_t)k * m + k];
+    for (int j = t; j < m; j += nt) {
+      const double v = A[(int64_t)k * m + j] * inv;
+      A[(int64_t)k * m + j] = v;
+      col[j] = v;
+    }
+    __syncthreads();
+    const int r = m - k - 1;
+    for (int64_t idx = t; idx < (int64_t)r * m; idx += nt) {
+      const int i = k + 1 + (int)(idx / m), j = (int)(idx % m);
+      A[(int64_t)i * m + j] -= L[(int64_t)i * m + k] * col[j];
+    }
+    __syncthreads();
+  }
+  // ---- 2c. A <- A L^-T (column forward substitution) ----
+  for (int k = 0; k < m; ++k) {
+    const double inv = 1.0 / L[(int64_t)k * m + k];
+    for (int i = t; i < m; i += nt) {
+      const double v = A[(int64_t)i * m + k] * inv;
+      A[(int64_t)i * m + k] = v;
+      col[i] = v;
+    }
+    __syncthreads();
+    const int r = m - k - 1;
+    for (int64_t idx = t; idx < (int64_t)m * r; idx += nt) {
+      const int i = (int)(idx / r), j = k + 1 + (int)(idx % r);
+      A[(int64_t)i * m + j] -= L[(int64_t)j * m + k] * col[i];
+    }
+    __syncthreads();
+  }
+  // ---- 3. Householder reduction to Hessenberg form ----
+  for (int k = 0; k < m - 2; ++k) {
+    double part = 0.0;
+    for (int i = k + 2 + t; i < m; i += nt) {
+      const double v = A[(int64_t)i * m + k];
+      part += v * v;
+    }
+    const double sigma = block_sum(part, sh.red);
+    if (t == 0) {
+      const double x0 = A[(int64_t)(k + 1) * m + k];
+      if (sigma == 0.0) {
+        sh.scal[1] = 0.0;
+        sh.scal[2] = 1.0;
+      } else {
+        const double mu = sqrt(x0 * x0 + sigma);
+        const double v0 = (x0 <= 0.0) ? (x0 - mu) : (-sigma / (x0 + mu));
+        sh.scal[1] = 2.0 * v0 * v0 / (sigma + v0 * v0);
+        sh.scal[2] = v0;
+      }
+    }
+    __syncthreads();
+    const double beta = sh.scal[1], v0 = sh.scal[2];
+    if (t == 0) hbeta[k] = beta;
+    // u = (1, x[1:]/v0) into col[k+1..m-1]
+    for (int i = k + 1 + t; i < m; i += nt) col[i] = (i == k + 1) ? 1.0 : A[(int64_t)i * m + k] / v0;
+    __syncthreads();
+    if (beta != 0.0) {
+      // left: rows k+1.., columns k.. (column-owned)
+      for (int j = k + t; j < m; j += nt) {
+        double wj = 0.0;
+        for (int i = k + 1; i < m; ++i) wj += col[i] * A[(int64_t)i * m + j];
+        wj *= beta;
+        for (int i = k + 1; i < m; ++i) A[(int64_t)i * m + j] -= wj * col[i];
+      }
+      __syncthreads();
+      // right: all rows, columns k+1.. (warp per row)
+      const int lane = t & 31, wid = t >> 5, nw = nt >> 5;
+      for (int i = wid; i < m; i += nw) {
+        double zi = 0.0;
+        for (int j = k + 1 + lane; j < m; j += 32) zi += A[(int64_t)i * m + j] * col[j];
+        for (int o = 16; o > 0; o >>= 1) zi += __shfl_xor_sync(0xffffffffu, zi, o);
+        zi *= beta;
+        for (int j = k + 1 + lane; j < m; j += 32) A[(int64_t)i * m + j] -= zi * col[j];
+      }
+      __syncthreads();
+    }
+    // store the reflector below the subdiagonal
+    for (int i = k + 2 + t; i < m; i += nt) A[(int64_t)i * m + k] = col[i];
+    __syncthreads();
+  }
+  // ---- Hessenberg copies: Hh (full) and the band store in shared or global memory ----
+  double amx = 0.0;
+  for (int64_t idx = t; idx < mm; idx += nt) {
+    const int i = (int)(idx / m), j = (int)(idx % m);
+    const double v = (j >= i - 1) ? A[idx] : 0.0;
+    Hh[idx] = v;
+    amx = fmax(amx, fabs(v));
+  }
+  const double anorm = fmax(block_max(amx, sh.red), 1e-300);
+  const int64_t bsize = Band::size(m);
+  const bool in_smem = (bsize * 8 <= (int64_t)200 * 1024);
+  Band band{in_smem ? dsm : W, m};
+  for (int i = t; i < m; i += nt) {
+    const int c0 = i > 3 ? i - 3 : 0;
+    for (int j = c0; j < m; ++j) band.at(i, j) = (j >= i - 1) ? Hh[(int64_t)i * m + j] : 0.0;
+  }
+  __syncthreads();
+  // ---- 4. eigenvalues ----
+  const bool ok = hqr_eigenvalues(band, m, wr, wi, anorm, sh);
+  __syncthreads();
+  if (!ok) {
+    if (t == 0) *pb.status = ST_NOCONV;
+    return;
+  }
+  // ---- selection of the lowest real parts ----
+  if (t == 0) {
+    int nsel = 0;
+    const int want = pb.mode == 1 ? 1 : pb.k;
+    // repeated minimum search (small k)
+    for (int i = 0; i < m; ++i) vtmp[i] = 0.0;   // used flags
+    while (nsel < want) {
+      int best = -1;
+      double bv = 0.0;
+      for (int i = 0; i < m; ++i) {
+        if (vtmp[i] != 0.0) continue;
+        if (best < 0 || wr[i] < bv) {
+          best = i;
+          bv = wr[i];
+        }
+      }
+      if (best < 0) break;
+      vtmp[best] = 1.0;
+      if (wi[best] != 0.0) {
+        // mark the conjugate partner (adjacent from the 2 x 2 block)
+        int partner = -1;
+        if (best + 1 < m && wi[best + 1] == -wi[best] && wr[best + 1] == wr[best]) partner = best + 1;
+        if (best > 0 && wi[best - 1] == -wi[best] && wr[best - 1] == wr[best]) partner = best - 1;
+        if (partner >= 0) vtmp[partner] = 1.0;
+        const int pos = wi[best] > 0.0 ? best : (partner >= 0 ? partner : best);
+        sh.sel_idx[nsel] = pos;
+        sh.sel_part[nsel] = 1;
+        ++nsel;
+        if (nsel < want) {
+          sh.sel_idx[nsel] = pos;
+          sh.sel_part[nsel] = 2;
+          ++nsel;
+        }
+      } else {
+        sh.sel_idx[nsel] = best;
+        sh.sel_part[nsel] = 0;
+        ++nsel;
+      }
+    }
+    sh.iscal[2] = nsel;
+    if (pb.mode == 1 && nsel > 0 && sh.sel_part[0] != 0) sh.iscal[1] = ST_COMPLEX;
+  }
+  __syncthreads();
+  if (sh.iscal[1] != ST_OK) {
+    if (t == 0) *pb.status = sh.iscal[1];
+    return;
+  }
+  const int nsel = sh.iscal[2];
+  // ---- 5./6. eigenvectors ----
+  // W is free after each inverse iteration: W[0, m) and W[m, 2m) hold the back-transformed real
+  // and imaginary parts.  A complex eigenvector is rotated so that its largest-magnitude
+  // component is real and positive; its real part (kept alone when N_K ends inside the pair)
+  // is then well defined.
+  double* vr = W;
+  double* vi = W + m;
+  int last_idx = -1;
+  for (int q = 0; q < nsel; ++q) {
+    const int idx = sh.sel_idx[q];
+    const int part = sh.sel_part[q];
+    if (idx != last_idx) {
+      hess_inverse_iteration(Hh, m, wr[idx], part ? wi[idx] : 0.0, anorm, W, yr, yi, plr, pli,
+                             pswap, sh);
+      for (int i = t; i < m; i += nt) {
+        vr[i] = yr[i];
+        vi[i] = yi[i];
+      }
+      __syncthreads();
+      back_transform(A, hbeta, L, dsc, m, vr, sh);
+      if (part) {
+        back_transform(A, hbeta, L, dsc, m, vi, sh);
+        if (t == 0) {
+          int best = 0;
+          double bv = -1.0;
+          for (int i = 0; i < m; ++i) {
+            const double a = vr[i] * vr[i] + vi[i] * vi[i];
+            if (a > bv) {
+              bv = a;
+              best = i;
+            }
+          }
+          const double nr = sqrt(bv);
+          sh.scal[6] = vr[best] / nr;
+          sh.scal[7] = vi[best] / nr;
+        }
+        __syncthreads();
+        const double c = sh.scal[6], s = sh.scal[7];
+        for (int i = t; i < m; i += nt) {
+          const double a = vr[i], b = vi[i];
+          vr[i] = a * c + b * s;       // (a + i b)(c - i s)
+          vi[i] = b * c - a * s;
+        }
+        __syncthreads();
+      }
+      last_idx = idx;
+    }
+    double* out = pb.vec + (int64_t)q * m;
+    const double* src = (part == 2) ? vi : vr;
+    for (int i = t; i < m; i += nt) out[i] = src[i];
+    if (t == 0) pb.lam[q] = wr[idx];
+    __syncthreads();
+  }
+  if (t == 0) *pb.status = (nsel == (pb.mode == 1 ? 1 : pb.k)) ? ST_OK : ST_NOCONV;
+}
+
+}  // namespace
+
+size_t eig_work_doubles(int64_t m) { return (size_t)(5 * m * m + 16 * m); }
+
+void launch_eig(const EigProblem* probs, int nprob, int threads, cudaStream_t st) {
+  if (nprob <= 0) return;
+  (void)threads;
+  const int smem = 200 * 1024;
+  cudaFuncSetAttribute(eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  eig_kernel<<<nprob, kEigThreads, smem, st>>>(probs);
+}
+
+}  // namespace blm

@@ -1,0 +1,159 @@
+// Internal declarations shared by the library's translation units (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/blm.h"
+
+namespace blm {
+
+// ---------------------------------------------------------------------------------------------
+// Operand segments of the sample contractions.  A segment is a run of columns of one of two
+// sample-major sources (src 0: the caller's sample arrays O, G; src 1: the handle's projection
+// scratch Y, Z).  Its value for sample s, column c is
+//   plain:  Y[s, col0 + c] - shift[col0 + c]
+//   xform:  E[s] * (Y[s, col0 + c] - shift[col0 + c]) + Z[s, col0 + c]
+// which are the ratios <n|Psibar^x>/<n|Psi> (up to the constant shift) and <n|H Psibar^x>/<n|Psi>
+// of Eq. 3 when Y = O, Z = dE_L/dmu.  The shift applies to src 0 only.
+// ---------------------------------------------------------------------------------------------
+struct Seg {
+  int32_t src;
+  int32_t xform;
+  int64_t col0;
+};
+
+struct SrcArgs {
+  const double* Y[2];
+  const double* Z[2];
+  int64_t ld[2];
+  const double* shift;
+  const double* E;
+  const double* w;
+};
+
+// One 64 x 64 output tile: C[a0 + i, b0 + j] += sum_s w_s A(s, a0 + i) B(s, b0 + j),
+// i < a_n, j < b_n, A from segment a_seg, B from segment b_seg; out points at C[a0, b0].
+struct Tile {
+  int32_t a_seg, b_seg;
+  int32_t a0, b0;
+  int32_t a_n, b_n;
+  int32_t pad0, pad1;
+  double* out;
+  int64_t out_ld;
+};
+
+// Projection of every sample onto per-block directions:
+//   Y[s, oc + j] = sum_i dir[j, i] (O[s, lo + i] - shift[lo + i]) - cen[oc + j]
+//   Z[s, oc + j] = sum_i dir[j, i] G[s, lo + i]
+struct ProjBlock {
+  int64_t lo;        // first parameter of the block
+  int32_t m;         // parameters in the block
+  int32_t nd;        // directions
+  int32_t oc;        // first output column
+  int32_t pad;
+  const double* dir; // nd rows of m values, row stride dld
+  int64_t dld;
+};
+
+enum { ST_OK = 0, ST_NOT_PD = 1, ST_NONFINITE = 2, ST_COMPLEX = 3, ST_NOCONV = 4, ST_ALPHA = 5,
+       ST_ZERO_DIR = 6 };
+
+// ------------------------------- launchers (blm_sweep_f64.cu) --------------------------------
+template <typename T>
+void launch_colmean(const T* O, int64_t ns, int64_t ld, int64_t n, double* sum_out,
+                    cudaStream_t st);
+template <typename T>
+void launch_sums(const T* Y, const T* Z, const T* E, const T* w, int64_t ns, int64_t ldy,
+                 int64_t ldz, int64_t ncols, const double* shift, double* sY, double* sEY,
+                 double* sZ, double* scal /* [sw, sE] or NULL */, bool fp32_runs,
+                 cudaStream_t st);
+void launch_contract(const Seg* segs, const Tile* tiles, int ntiles, const SrcArgs& src,
+                     int64_t ns, int splits, cudaStream_t st);
+template <typename T, typename TO>
+void launch_project(const T* O, const T* G, int64_t ldo, int64_t ldg, const double* shift,
+                    const ProjBlock* blocks, int nblocks, const double* cen, TO* Y, TO* Z,
+                    int64_t ldout, int64_t ns, int max_m, int max_nd, cudaStream_t st);
+
+// ------------------------------- launchers (blm_sweep_tc.cu) ---------------------------------
+// Split-BF16 tcgen05 accumulation: for each tile, rows [row0, row0 + 128) and columns
+// [col0, col0 + 256) of C_b = sum_s w_s Y'_b [Y'_b | E Y'_b + Z_b]^T  (Y' = Y - shift; the block
+// is columns [lo, lo + m) of Y and Z; out is C_b, m x 2m row-major FP64, accumulated into).
+struct TcTile {
+  int64_t lo;
+  int32_t m;
+  int32_t row0;
+  int32_t col0;
+  int32_t pad;
+  double* out;
+};
+bool tc_supported();
+cudaError_t launch_tc_accumulate(const float* Y, const float* Z, const float* E, const float* w,
+                                 int64_t ns, int64_t ld, const float* shift32,
+                                 const TcTile* tiles, int ntiles, int32_t* err, cudaStream_t st);
+
+// ------------------------------- launchers (blm_assemble.cu) ---------------------------------
+struct BlockAsm {
+  int64_t lo;          // first parameter
+  int32_t m;           // M_b
+  int32_t d;           // tangent dimension M_b + N_O (N_B - 1)
+  int32_t b;           // block index
+  int32_t pad;
+  const double* C;     // M_b x 2 M_b sums  [O'O'^T | O'X'^T]
+  double* S;           // (1+d)^2 output
+  double* H;           // (1+d)^2 output
+};
+struct HistSums {      // history sums (N_O > 0), R = N_O * N_B virtual columns t_jk, r = j*N_B+k
+  int32_t n_old, n_blocks;
+  const double* OT;    // n x 2R: [sum w O' T' | sum w O' (E T' + U)]
+  const double* XT;    // n x R : sum w X' T'
+  const double* TT;    // R x 2R: [sum w T' T' | sum w T' (E T' + U)]
+  const double* sT;    // R: sum w T'
+  const double* sET;   // R: sum w E T'
+  const double* sU;    // R: sum w U
+  const double* gram;  // R x R: D_jk . D_j'k' (zero unless k == k')
+};
+void launch_assemble_blocks(const BlockAsm* blocks, int nblocks, int max_dim, const double* sO,
+                            const double* sEO, const double* sG, const double* scal,
+                            HistSums hist, double shift, cudaStream_t st);
+void launch_assemble_combined(int64_t dc, const double* C, const double* sY, const double* sEY,
+                              const double* sZ, const double* scal, const double* gram,
+                              double shift, double* S, double* H, cudaStream_t st);
+
+// ------------------------------- launchers (blm_eig.cu) --------------------------------------
+struct EigProblem {
+  int32_t m;           // dimension (1 + tangent)
+  int32_t k;           // directions wanted (lowest real parts)
+  int32_t mode;        // 0: block (complex pair -> Re, Im), 1: combined (lowest must be real)
+  int32_t pad;
+  const double* S;     // m x m row-major
+  const double* H;     // m x m row-major
+  double* work;        // 5 m^2 + 16 m doubles
+  double* lam;         // k outputs (real parts)
+  double* vec;         // k x m outputs (real eigenvectors in the original basis)
+  int32_t* status;     // one word
+};
+void launch_eig(const EigProblem* probs, int nprob, int threads, cudaStream_t st);
+size_t eig_work_doubles(int64_t m);
+
+// ------------------------------- launchers (blm_update.cu) -----------------------------------
+struct DirBlock {       // block solve -> B rows
+  int32_t m;            // M_b
+  int32_t k;            // kept
+  int32_t d1;           // 1 + d_b (eigenvector length)
+  int32_t pad;
+  const double* vec;    // k x d1 eigenvectors
+  double* B;            // k x M_b output rows
+  int32_t* status;
+};
+void launch_extract_dirs(const DirBlock* blocks, int nblocks, cudaStream_t st);
+void launch_cen(const ProjBlock* blocks, int nblocks, const double* sO, const double* scal,
+                double* cen, cudaStream_t st);
+void launch_gram(const ProjBlock* blocks, int nblocks, int max_nd, double* gram, int64_t ld,
+                 cudaStream_t st);
+void launch_update(int nblocks, const ProjBlock* blocks, int64_t dc, const double* c,
+                   const double* shift, const double* sO, const double* scal, double* alpha,
+                   double* dmu, int32_t* status, cudaStream_t st);
+
+}  // namespace blm

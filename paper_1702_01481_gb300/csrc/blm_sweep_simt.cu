@@ -1,0 +1,331 @@
+// Sample sweeps on CUDA cores: reference shift, first-moment sums, tiled sample contractions
+// and projections onto per-block directions.  These kernels form the plain FP64 path of the
+// step (FP64 inputs) and the non-contraction parts of the mixed path (FP32 inputs).
+//
+// Eq. 3 (Sec. II.A): every matrix element is a weighted sum over samples of a product of two
+// per-sample ratios; with the per-parameter reference shift c the sums are taken over
+// O' = O - c and X' = E O' + G, and blm_assemble.cu turns them into centred matrices.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "blm_internal.cuh"
+
+namespace blm {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------------------------------------
+// Column sums of O over a sample range (the first chunk's mean becomes the reference shift).
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+colsum_kernel(const T* __restrict__ O, int64_t ns, int64_t ld, int64_t n, int64_t per_split,
+              double* __restrict__ out) {
+  const int64_t col = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (col >= n) return;
+  const int64_t s0 = (int64_t)blockIdx.y * per_split;
+  const int64_t s1 = min(ns, s0 + per_split);
+  double acc = 0.0;
+  for (int64_t s = s0; s < s1; ++s) acc += (double)O[s * ld + col];
+  atomicAdd(out + col, acc);
+}
+
+// ---------------------------------------------------------------------------------------------
+// First moments: sY += w (Y - shift), sEY += w E (Y - shift), sZ += w Z per column; and the
+// scalars [sum w, sum w E] when scal != NULL.  FP32 inputs are summed in FP32 over runs of
+// 32 samples and the run sums added in FP64 when A = float (the mixed path, whose O' is the
+// FP32 value O - c); with A = double everything is FP64 (the FP64 path).
+// ---------------------------------------------------------------------------------------------
+template <typename T, typename A>
+__global__ void __launch_bounds__(kThreads)
+sums_kernel(const T* __restrict__ Y, const T* __restrict__ Z, const T* __restrict__ E,
+            const T* __restrict__ w, int64_t ns, int64_t ldy, int64_t ldz, int64_t ncols,
+            int64_t per_split, const double* __restrict__ shift, double* __restrict__ sY,
+            double* __restrict__ sEY, double* __restrict__ sZ, double* __restrict__ scal) {
+  const int64_t col = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  const int64_t s0 = (int64_t)blockIdx.y * per_split;
+  const int64_t s1 = min(ns, s0 + per_split);
+  if (scal != nullptr && blockIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int64_t s = s0 + threadIdx.x; s < s1; s += kThreads) {
+      const double ws = w ? (double)w[s] : 1.0;
+      a += ws;
+      b += ws * (double)E[s];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(scal + 0, a);
+      atomicAdd(scal + 1, b);
+    }
+  }
+  if (col >= ncols) return;
+  const A sh = shift ? (A)shift[col] : (A)0;
+  double dY = 0.0, dEY = 0.0, dZ = 0.0;
+  for (int64_t r = s0; r < s1; r += 32) {
+    const int64_t re = min(s1, r + 32);
+    A aY = 0, aEY = 0, aZ = 0;
+    for (int64_t s = r; s < re; ++s) {
+      const A ws = w ? (A)w[s] : (A)1;
+      const A y = (A)Y[s * ldy + col] - sh;
+      const A wy = ws * y;
+      aY += wy;
+      aEY += wy * (A)E[s];
+      if (Z) aZ += ws * (A)Z[s * ldz + col];
+    }
+    dY += (double)aY;
+    dEY += (double)aEY;
+    dZ += (double)aZ;
+  }
+  atomicAdd(sY + col, dY);
+  atomicAdd(sEY + col, dEY);
+  if (Z) atomicAdd(sZ + col, dZ);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Tiled FP64 contraction over samples: out[i, j] += sum_s w_s A(s, i) B(s, j), 64 x 64 tiles,
+// 16 samples per stage, 4 x 4 outputs per thread.  blockIdx.x = tile, blockIdx.y = sample split.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ double seg_value(const Seg& sg, const SrcArgs& a, int64_t s,
+                                            int64_t c) {
+  const int64_t col = sg.col0 + c;
+  const int64_t ld = a.ld[sg.src];
+  double y = a.Y[sg.src][s * ld + col];
+  if (sg.src == 0 && a.shift) y -= a.shift[col];
+  if (sg.xform) y = a.E[s] * y + a.Z[sg.src][s * ld + col];
+  return y;
+}
+
+__global__ void __launch_bounds__(kThreads)
+contract_kernel(const Seg* __restrict__ segs, const Tile* __restrict__ tiles, SrcArgs src,
+                int64_t ns, int64_t per_split) {
+  __shared__ double As[16][64];
+  __shared__ double Bs[16][64];
+  const Tile tl = tiles[blockIdx.x];
+  const Seg sa = segs[tl.a_seg];
+  const Seg sb = segs[tl.b_seg];
+  const int64_t s0 = (int64_t)blockIdx.y * per_split;
+  const int64_t s1 = min(ns, s0 + per_split);
+  const int t = threadIdx.x;
+  const int tx = t & 15, ty = t >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+
+  for (int64_t sb0 = s0; sb0 < s1; sb0 += 16) {
+    for (int idx = t; idx < 16 * 64; idx += kThreads) {
+      const int k = idx >> 6, c = idx & 63;
+      const int64_t s = sb0 + k;
+      double av = 0.0, bv = 0.0;
+      if (s < s1) {
+        if (c < tl.a_n) av = seg_value(sa, src, s, tl.a0 + c);
+        if (c < tl.b_n) {
+          bv = seg_value(sb, src, s, tl.b0 + c);
+          if (src.w) bv *= src.w[s];
+        }
+      }
+      As[k][c] = av;
+      Bs[k][c] = bv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      double a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[k][ty * 4 + r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[k][tx * 4 + c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = ty * 4 + r;
+    if (i >= tl.a_n) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = tx * 4 + c;
+      if (j < tl.b_n) atomicAdd(tl.out + (int64_t)i * tl.out_ld + j, acc[r][c]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Projection onto per-block directions (Eq. 6 ratios p = Obar_b . B_j and r = G_b . B_j; the
+// same kernel gives the history projections t = O'_k . D_jk, u = G_k . D_jk of Eq. 9).
+// blockIdx.x = 32-sample tile, blockIdx.y = block; the block's parameters are taken in runs of
+// 128 through shared memory.
+// ---------------------------------------------------------------------------------------------
+constexpr int kPS = 32;   // samples per CTA
+constexpr int kPC = 128;  // parameters per shared-memory run
+
+template <typename T, typename A, typename TO>
+__global__ void __launch_bounds__(kThreads)
+project_kernel(const T* __restrict__ O, const T* __restrict__ G, int64_t ldo, int64_t ldg,
+               const double* __restrict__ shift, const ProjBlock* __restrict__ blocks,
+               const double* __restrict__ cen, TO* __restrict__ Y, TO* __restrict__ Z,
+               int64_t ldout, int64_t ns, int max_nd) {
+  extern __shared__ unsigned char smem_raw[];
+  A* Os = reinterpret_cast<A*>(smem_raw);          // kPS x kPC
+  A* Gs = Os + kPS * kPC;                          // kPS x kPC
+  A* Ds = Gs + kPS * kPC;                          // max_nd x kPC
+  const ProjBlock pb = blocks[blockIdx.y];
+  const int64_t s_base = (int64_t)blockIdx.x * kPS;
+  const int t = threadIdx.x;
+  const int npairs = kPS * pb.nd;                  // (sample, direction) pairs
+  // up to 8 pairs per thread (kPS * max_nd <= 8 * kThreads is checked by the launcher)
+  A accY[8], accZ[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) accY[q] = accZ[q] = (A)0;
+
+  for (int p0 = 0; p0 < pb.m; p0 += kPC) {
+    const int pc = min(kPC, pb.m - p0);
+    for (int idx = t; idx < kPS * kPC; idx += kThreads) {
+      const int k = idx / kPC, c = idx % kPC;
+      const int64_t s = s_base + k;
+      A ov = (A)0, gv = (A)0;
+      if (s < ns && c < pc) {
+        const int64_t col = pb.lo + p0 + c;
+        ov = (A)O[s * ldo + col] - (shift ? (A)shift[col] : (A)0);
+        gv = (A)G[s * ldg + col];
+      }
+      Os[idx] = ov;
+      Gs[idx] = gv;
+    }
+    for (int idx = t; idx < pb.nd * kPC; idx += kThreads) {
+      const int j = idx / kPC, c = idx % kPC;
+      Ds[idx] = (c < pc) ? (A)pb.dir[(int64_t)j * pb.dld + p0 + c] : (A)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int pair = t + q * kThreads;
+      if (pair < npairs) {
+        const int k = pair / pb.nd, j = pair % pb.nd;
+        const A* o = Os + k * kPC;
+        const A* g = Gs + k * kPC;
+        const A* d = Ds + j * kPC;
+        A y = accY[q], z = accZ[q];
+        for (int c = 0; c < pc; ++c) {
+          y = fma(d[c], o[c], y);
+          z = fma(d[c], g[c], z);
+        }
+        accY[q] = y;
+        accZ[q] = z;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int pair = t + q * kThreads;
+    if (pair < npairs) {
+      const int k = pair / pb.nd, j = pair % pb.nd;
+      const int64_t s = s_base + k;
+      if (s < ns) {
+        const int64_t oc = pb.oc + j;
+        A y = accY[q];
+        if (cen) y -= (A)cen[oc];
+        Y[s * ldout + oc] = (TO)y;
+        Z[s * ldout + oc] = (TO)accZ[q];
+      }
+    }
+  }
+}
+
+int splits_for(int64_t ns, int64_t granule, int64_t max_splits) {
+  int64_t s = (ns + granule - 1) / granule;
+  if (s > max_splits) s = max_splits;
+  if (s < 1) s = 1;
+  return (int)s;
+}
+
+}  // namespace
+
+template <typename T>
+void launch_colmean(const T* O, int64_t ns, int64_t ld, int64_t n, double* sum_out,
+                    cudaStream_t st) {
+  if (ns <= 0) return;
+  const int splits = splits_for(ns, 512, 256);
+  const int64_t per = (ns + splits - 1) / splits;
+  dim3 grid((unsigned)((n + kThreads - 1) / kThreads), (unsigned)splits);
+  colsum_kernel<T><<<grid, kThreads, 0, st>>>(O, ns, ld, n, per, sum_out);
+}
+
+template <typename T>
+void launch_sums(const T* Y, const T* Z, const T* E, const T* w, int64_t ns, int64_t ldy,
+                 int64_t ldz, int64_t ncols, const double* shift, double* sY, double* sEY,
+                 double* sZ, double* scal, bool fp32_runs, cudaStream_t st) {
+  if (ns <= 0) return;
+  const int64_t colblocks = (ncols + kThreads - 1) / kThreads;
+  const int splits = splits_for(ns, 256, (int64_t)4 * 152 * 4 / (colblocks > 0 ? colblocks : 1) + 1);
+  const int64_t per = ((ns + splits - 1) / splits + 31) / 32 * 32;
+  dim3 grid((unsigned)(colblocks > 0 ? colblocks : 1), (unsigned)splits);
+  if (fp32_runs)
+    sums_kernel<T, float><<<grid, kThreads, 0, st>>>(Y, Z, E, w, ns, ldy, ldz, ncols, per, shift,
+                                                     sY, sEY, sZ, scal);
+  else
+    sums_kernel<T, double><<<grid, kThreads, 0, st>>>(Y, Z, E, w, ns, ldy, ldz, ncols, per, shift,
+                                                      sY, sEY, sZ, scal);
+}
+
+void launch_contract(const Seg* segs, const Tile* tiles, int ntiles, const SrcArgs& src,
+                     int64_t ns, int splits, cudaStream_t st) {
+  if (ns <= 0 || ntiles <= 0) return;
+  if (splits < 1) splits = 1;
+  int64_t per = (ns + splits - 1) / splits;
+  per = (per + 15) / 16 * 16;
+  splits = (int)((ns + per - 1) / per);
+  dim3 grid((unsigned)ntiles, (unsigned)splits);
+  contract_kernel<<<grid, kThreads, 0, st>>>(segs, tiles, src, ns, per);
+}
+
+template <typename T, typename TO>
+void launch_project(const T* O, const T* G, int64_t ldo, int64_t ldg, const double* shift,
+                    const ProjBlock* blocks, int nblocks, const double* cen, TO* Y, TO* Z,
+                    int64_t ldout, int64_t ns, int max_m, int max_nd, cudaStream_t st) {
+  (void)max_m;
+  if (ns <= 0 || nblocks <= 0) return;
+  using A = TO;   // FP64 path: FP64 throughout; mixed path: FP32 products and sums
+  const size_t smem = sizeof(A) * (size_t)(2 * kPS * kPC + max_nd * kPC);
+  cudaFuncSetAttribute(project_kernel<T, A, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  dim3 grid((unsigned)((ns + kPS - 1) / kPS), (unsigned)nblocks);
+  project_kernel<T, A, TO><<<grid, kThreads, smem, st>>>(O, G, ldo, ldg, shift, blocks, cen, Y, Z,
+                                                         ldout, ns, max_nd);
+}
+
+template void launch_colmean<double>(const double*, int64_t, int64_t, int64_t, double*,
+                                     cudaStream_t);
+template void launch_colmean<float>(const float*, int64_t, int64_t, int64_t, double*,
+                                    cudaStream_t);
+template void launch_sums<double>(const double*, const double*, const double*, const double*,
+                                  int64_t, int64_t, int64_t, int64_t, const double*, double*,
+                                  double*, double*, double*, bool, cudaStream_t);
+template void launch_sums<float>(const float*, const float*, const float*, const float*, int64_t,
+                                 int64_t, int64_t, int64_t, const double*, double*, double*,
+                                 double*, double*, bool, cudaStream_t);
+template void launch_project<double, double>(const double*, const double*, int64_t, int64_t,
+                                             const double*, const ProjBlock*, int, const double*,
+                                             double*, double*, int64_t, int64_t, int, int,
+                                             cudaStream_t);
+template void launch_project<float, float>(const float*, const float*, int64_t, int64_t,
+                                           const double*, const ProjBlock*, int, const double*,
+                                           float*, float*, int64_t, int64_t, int, int,
+                                           cudaStream_t);
+template void launch_project<float, double>(const float*, const float*, int64_t, int64_t,
+                                            const double*, const ProjBlock*, int, const double*,
+                                            double*, double*, int64_t, int64_t, int, int,
+                                            cudaStream_t);
+
+}  // namespace blm

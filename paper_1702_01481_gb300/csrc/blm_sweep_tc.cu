@@ -1,0 +1,532 @@
+// Split-BF16 sample contraction on tcgen05 tensor cores (sm_103a).
+//
+// Computes, for each tile of 128 rows x 256 columns of a block's sums (Eq. 3),
+//   C_b[r, c] += sum_s  A(s, r) B(s, c),   A = Y'_b,   B = w * [Y'_b | E Y'_b + Z_b]
+// with Y' = Y - shift (first sweep: Y = O, Z = dE_L/dmu; second sweep: Y = p, Z = r of Eq. 6).
+// Each FP32 operand value v is split as v = hi + lo + O(2^-16 v) with hi = bf16(v),
+// lo = bf16(v - hi); the four products hi*hi + hi*lo + lo*hi + lo*lo are accumulated by
+// tcgen05.mma (kind::f16, BF16 inputs, FP32 accumulator in tensor memory).
+//
+// Accumulation precision: the tensor-memory accumulator (L1, 256 columns) is restarted every
+// `flush_stages` stages of 64 samples; the epilogue warps then add it into a second FP32
+// accumulator in tensor memory (L2, 256 columns, round-to-nearest CUDA-core adds), and at the end
+// of each work unit add L1 + L2 into the FP64 result with atomics.  Short L1 intervals bound the
+// rounding of the tensor core's FP32 accumulation; the FP64 atomics bound the sum across units.
+//
+// Work units are (sample range, tile) pairs; a persistent grid of one CTA per SM walks them.
+// Roles per CTA (16 warps): warp 0 allocates tensor memory and one lane issues the MMAs;
+// warps 4-7 are the epilogue (one per 32-lane tensor-memory quadrant); the other 11 warps
+// convert FP32 samples into the split-BF16 operands in shared memory (K-major, 128-byte
+// swizzle: each operand row holds 64 consecutive samples of one parameter).
+// Every wait on an mbarrier is bounded; on timeout the kernel records an error code, drains its
+// own MMAs, frees tensor memory and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+
+#include "blm_internal.cuh"
+
+namespace blm {
+
+namespace {
+
+constexpr int kWarps = 16;
+constexpr int kThreads = kWarps * 32;
+constexpr int kStageK = 64;                       // samples per stage
+constexpr int kStages = 2;
+constexpr int kBRows = 256;
+constexpr int kARows = 128;
+constexpr int kBBytes = kBRows * 128;             // one split half of B: 32 KB
+constexpr int kABytes = kARows * 128;             // one split half of A: 16 KB
+constexpr int kStageBytes = 2 * kBBytes + 2 * kABytes;
+constexpr int kConvWarps = 11;
+constexpr int kBarOffset = kStages * kStageBytes;
+constexpr int kSmemBytes = kBarOffset + 256 + 1024;   // + barriers + alignment slack
+constexpr uint32_t kWaitLimit = 1u << 24;          // polls (each try_wait may suspend briefly)
+
+enum { A_VIEW = 0, A_FROM_B = 1, A_SEPARATE = 2 };
+
+struct Bars {
+  uint64_t op_full[kStages];
+  uint64_t op_empty[kStages];
+  uint64_t l1_full;
+  uint64_t l1_empty;
+  uint64_t drain;
+  uint32_t tmem_base;
+  int32_t abort;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ uint32_t mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok;
+}
+
+// Bounded wait: returns false (after recording `code`) if the phase never completes or another
+// role has already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, Bars* bars, int32_t* err,
+                                          int code) {
+  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*(volatile int32_t*)&bars->abort) return false;
+  }
+  *(volatile int32_t*)&bars->abort = 1;
+  atomicExch(err, code);
+  return false;
+}
+
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of 128 bytes,
+// 8-row groups 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);            // start address
+  d |= (uint64_t)1u << 16;                           // leading byte offset (unused here)
+  d |= (uint64_t)(1024u >> 4) << 32;                 // stride byte offset
+  d |= (uint64_t)1u << 46;                           // version
+  d |= (uint64_t)2u << 61;                           // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = 128, N = 256.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) |
+                            ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+#define TMEM_LD32(taddr, r)                                                                       \
+  asm volatile(                                                                                   \
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"    \
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"          \
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),       \
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),   \
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),            \
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),            \
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])             \
+      : "r"(taddr))
+
+#define TMEM_ST32(taddr, r)                                                                       \
+  asm volatile(                                                                                   \
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13," \
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(     \
+          taddr),                                                                                 \
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),     \
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),          \
+      "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),        \
+      "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),        \
+      "r"(r[29]), "r"(r[30]), "r"(r[31])                                                          \
+      : "memory")
+
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// bf16x2 packing: the first element goes to the low half (lower address).
+__device__ __forceinline__ uint32_t pack2(float first, float second) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(second), "f"(first));
+  return d;
+}
+
+// Split 8 values into hi/lo bf16 (4 words each).
+__device__ __forceinline__ void split8(const float* v, uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t hh = pack2(v[2 * k], v[2 * k + 1]);
+    const float h0 = __uint_as_float(hh << 16);
+    const float h1 = __uint_as_float(hh & 0xFFFF0000u);
+    h[k] = hh;
+    l[k] = pack2(v[2 * k] - h0, v[2 * k + 1] - h1);
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y),
+               "r"(v.z), "r"(v.w)
+               : "memory");
+}
+
+// Byte offset of (row, 16-byte chunk) in a K-major 128-byte-swizzled operand tile.
+__device__ __forceinline__ uint32_t swz(int row, int chunk) {
+  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
+}
+
+struct TileInfo {
+  int64_t lo;
+  int m, row0, col0, pb, nB, nA, xtype, amode;
+  double* out;
+};
+
+// A is a view of B's rows only when both hold the same unweighted Y' values.
+__device__ __forceinline__ TileInfo decode_tile(const TcTile& t, bool weighted) {
+  TileInfo ti;
+  ti.lo = t.lo;
+  ti.m = t.m;
+  ti.row0 = t.row0;
+  ti.col0 = t.col0;
+  ti.out = t.out;
+  ti.xtype = t.col0 >= t.m;
+  ti.pb = ti.xtype ? t.col0 - t.m : t.col0;
+  ti.nB = min(kBRows, (ti.xtype ? 2 * t.m : t.m) - t.col0);
+  ti.nA = min(kARows, t.m - t.row0);
+  if (!weighted && !ti.xtype && ti.pb <= ti.row0 && ti.row0 + kARows <= ti.pb + kBRows)
+    ti.amode = A_VIEW;
+  else if (ti.xtype && ti.pb <= ti.row0 && ti.row0 + kARows <= ti.pb + ti.nB)
+    ti.amode = A_FROM_B;
+  else
+    ti.amode = A_SEPARATE;
+  return ti;
+}
+
+struct Params {
+  const float* Y;
+  const float* Z;
+  const float* E;
+  const float* w;
+  const float* shift;
+  int64_t ns;
+  int64_t ld;
+  const TcTile* tiles;
+  int ntiles;
+  int64_t range_len;     // samples per unit (multiple of kStageK)
+  int64_t nunits;
+  int flush_stages;
+  int32_t* err;
+};
+
+// Converter job: 32 operand rows x 32 samples.  Lane = 8 g + l: sample group g (8 samples),
+// rows l + 8 e (e = 0..3) -> conflict-free 16-byte swizzled stores, 32-byte load sectors.
+// kind 0: B rows (Y' or X', weighted; A rows too in A_FROM_B mode); kind 1: A rows (Y').
+__device__ __forceinline__ void convert_job(const Params& P, const TileInfo& ti, int kind,
+                                            int rowgroup, int half, int64_t stage_base,
+                                            int64_t s_end, uint8_t* stage) {
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 3, l = lane & 7;
+  const int64_t s0 = stage_base + 32 * half + 8 * g;
+  float ev[8], wv[8];
+  bool vs[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int64_t s = s0 + q;
+    vs[q] = s < s_end;
+    ev[q] = (kind == 0 && ti.xtype && vs[q]) ? P.E[s] : 0.0f;
+    wv[q] = (kind == 0 && P.w && vs[q]) ? P.w[s] : 1.0f;
+  }
+  const int chunk = 4 * half + g;
+  const uint32_t sbase = smem_u32(stage);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int row = rowgroup * 32 + l + 8 * e;
+    int64_t p;
+    bool vr;
+    if (kind == 0) {
+      vr = row < ti.nB;
+      p = ti.lo + ti.pb + row;
+    } else {
+      vr = row < ti.nA;
+      p = ti.lo + ti.row0 + row;
+    }
+    const float sh = (vr && P.shift) ? P.shift[p] : 0.0f;
+    float y[8], x[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const bool ok = vr && vs[q];
+      const int64_t idx = (s0 + q) * P.ld + p;
+      const float yy = ok ? P.Y[idx] - sh : 0.0f;
+      y[q] = yy;
+      if (kind == 0 && ti.xtype) {
+        const float zz = ok ? P.Z[idx] : 0.0f;
+        x[q] = fmaf(ev[q], yy, zz) * wv[q];
+      } else {
+        x[q] = yy * wv[q];
+      }
+    }
+    uint4 hi, lo;
+    const uint32_t off = swz(row, chunk);
+    if (kind == 0) {
+      split8(x, hi, lo);
+      st_shared_v4(sbase + off, hi);
+      st_shared_v4(sbase + kBBytes + off, lo);
+      if (ti.amode == A_FROM_B) {
+        const int arow = ti.pb + row - ti.row0;
+        if (arow >= 0 && arow < kARows) {
+          split8(y, hi, lo);
+          const uint32_t aoff = swz(arow, chunk);
+          st_shared_v4(sbase + 2 * kBBytes + aoff, hi);
+          st_shared_v4(sbase + 2 * kBBytes + kABytes + aoff, lo);
+        }
+      }
+    } else {
+      split8(y, hi, lo);
+      st_shared_v4(sbase + 2 * kBBytes + off, hi);
+      st_shared_v4(sbase + 2 * kBBytes + kABytes + off, lo);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) tc_accumulate_kernel(const Params P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  Bars* bars = (Bars*)(smem + kBarOffset);
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&bars->op_full[s], kConvWarps);
+      mbar_init(&bars->op_empty[s], 1);
+    }
+    mbar_init(&bars->l1_full, 1);
+    mbar_init(&bars->l1_empty, 4);
+    mbar_init(&bars->drain, 1);
+    bars->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     smem_u32(&bars->tmem_base))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;
+  const int fs = P.flush_stages;
+
+  if (warp == 0) {
+    // ------------------------------- MMA issuer -------------------------------
+    uint32_t g = 0, k = 0;
+    bool alive = true;
+    for (int64_t u = blockIdx.x; u < P.nunits && alive; u += gridDim.x) {
+      const TileInfo ti = decode_tile(P.tiles[u % P.ntiles], P.w != nullptr);
+      const int64_t sa = (u / P.ntiles) * P.range_len;
+      const int64_t sb = min(P.ns, sa + P.range_len);
+      const int nst = (int)((sb - sa + kStageK - 1) / kStageK);
+      for (int st = 0; st < nst && alive; ++st, ++g) {
+        const uint32_t slot = g % kStages, use = g / kStages;
+        uint32_t acc = 1;
+        if (st % fs == 0) {
+          alive = mbar_wait(&bars->l1_empty, (k & 1) ^ 1, bars, P.err, 11);
+          tc_fence_after();
+          acc = 0;
+        }
+        if (alive) alive = mbar_wait(&bars->op_full[slot], use & 1, bars, P.err, 12);
+        if (!alive) break;
+        tc_fence_after();
+        if (lane == 0) {
+          uint8_t* stage = smem + slot * kStageBytes;
+          const uint32_t bh = smem_u32(stage), bl = bh + kBBytes;
+          uint32_t ah, al;
+          if (ti.amode == A_VIEW) {
+            ah = bh + (uint32_t)(ti.row0 - ti.pb) * 128u;
+            al = bl + (uint32_t)(ti.row0 - ti.pb) * 128u;
+          } else {
+            ah = bh + 2 * kBBytes;
+            al = ah + kABytes;
+          }
+#pragma unroll
+          for (int ks = 0; ks < kStageK / 16; ++ks) {
+            const uint32_t o = ks * 32;
+            mma_bf16(tmem, sdesc(ah + o), sdesc(bh + o), acc);
+            mma_bf16(tmem, sdesc(ah + o), sdesc(bl + o), 1);
+            mma_bf16(tmem, sdesc(al + o), sdesc(bh + o), 1);
+            mma_bf16(tmem, sdesc(al + o), sdesc(bl + o), 1);
+            acc = 1;
+          }
+          mma_commit(&bars->op_empty[slot]);
+          if (st % fs == fs - 1 || st == nst - 1) mma_commit(&bars->l1_full);
+        }
+        __syncwarp();
+        if (st % fs == fs - 1 || st == nst - 1) ++k;
+      }
+    }
+    // drain: wait until every issued MMA has completed before tensor memory is released
+    if (lane == 0) mma_commit(&bars->drain);
+    __syncwarp();
+    for (uint32_t i = 0; i < kWaitLimit && !mbar_try_wait(&bars->drain, 0); ++i) {
+    }
+  } else if (warp >= 4 && warp < 8) {
+    // ------------------------------- epilogue ---------------------------------
+    const int q = warp & 3;                         // tensor-memory lane quadrant
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
+    uint32_t k = 0;
+    bool alive = true;
+    for (int64_t u = blockIdx.x; u < P.nunits && alive; u += gridDim.x) {
+      const TileInfo ti = decode_tile(P.tiles[u % P.ntiles], P.w != nullptr);
+      const int64_t sa = (u / P.ntiles) * P.range_len;
+      const int64_t sb = min(P.ns, sa + P.range_len);
+      const int nst = (int)((sb - sa + kStageK - 1) / kStageK);
+      const int nint = (nst + fs - 1) / fs;
+      for (int it = 0; it < nint; ++it, ++k) {
+        alive = mbar_wait(&bars->l1_full, k & 1, bars, P.err, 13);
+        if (!alive) break;
+        tc_fence_after();
+        const bool first = it == 0, last = it == nint - 1;
+        const int row = 32 * q + lane;
+        const bool vrow = row < ti.nA;
+        for (int cc = 0; cc < 256; cc += 32) {
+          uint32_t a[32], b[32];
+          TMEM_LD32(lane_addr + cc, a);
+          if (!first) TMEM_LD32(lane_addr + 256 + cc, b);
+          tmem_wait_ld();
+          if (last) {
+            if (vrow) {
+              double* orow = ti.out + (int64_t)(ti.row0 + row) * 2 * ti.m + ti.col0 + cc;
+              const int ncol = min(32, ti.nB - cc);
+#pragma unroll
+              for (int i = 0; i < 32; ++i) {
+                if (i < ncol) {
+                  const float v = __uint_as_float(a[i]) + (first ? 0.0f : __uint_as_float(b[i]));
+                  atomicAdd(orow + i, (double)v);
+                }
+              }
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              b[i] = first ? a[i] : __float_as_uint(__uint_as_float(a[i]) + __uint_as_float(b[i]));
+            TMEM_ST32(lane_addr + 256 + cc, b);
+          }
+        }
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars->l1_empty);
+      }
+    }
+  } else {
+    // ------------------------------- converters -------------------------------
+    const int cw = warp < 4 ? warp - 1 : warp - 5;   // 0 .. kConvWarps-1
+    uint32_t g = 0;
+    bool alive = true;
+    for (int64_t u = blockIdx.x; u < P.nunits && alive; u += gridDim.x) {
+      const TileInfo ti = decode_tile(P.tiles[u % P.ntiles], P.w != nullptr);
+      const int64_t sa = (u / P.ntiles) * P.range_len;
+      const int64_t sb = min(P.ns, sa + P.range_len);
+      const int nst = (int)((sb - sa + kStageK - 1) / kStageK);
+      const int njobs_b = (kBRows / 32) * 2;
+      const int njobs = njobs_b + (ti.amode == A_SEPARATE ? (kARows / 32) * 2 : 0);
+      for (int st = 0; st < nst; ++st, ++g) {
+        const uint32_t slot = g % kStages, use = g / kStages;
+        alive = mbar_wait(&bars->op_empty[slot], (use & 1) ^ 1, bars, P.err, 14);
+        if (!alive) break;
+        uint8_t* stage = smem + slot * kStageBytes;
+        const int64_t base = sa + (int64_t)st * kStageK;
+        for (int j = cw; j < njobs; j += kConvWarps) {
+          if (j < njobs_b)
+            convert_job(P, ti, 0, j >> 1, j & 1, base, sb, stage);
+          else
+            convert_job(P, ti, 1, (j - njobs_b) >> 1, (j - njobs_b) & 1, base, sb, stage);
+        }
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars->op_full[slot]);
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem)
+                 : "memory");
+  }
+}
+
+}  // namespace
+
+bool tc_supported() { return true; }
+
+cudaError_t launch_tc_accumulate(const float* Y, const float* Z, const float* E, const float* w,
+                                 int64_t ns, int64_t ld, const float* shift32,
+                                 const TcTile* tiles, int ntiles, int32_t* err,
+                                 cudaStream_t st) {
+  if (ns <= 0 || ntiles <= 0) return cudaSuccess;
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(tc_accumulate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kSmemBytes);
+  }
+  Params P;
+  P.Y = Y;
+  P.Z = Z;
+  P.E = E;
+  P.w = w;
+  P.shift = shift32;
+  P.ns = ns;
+  P.ld = ld;
+  P.tiles = tiles;
+  P.ntiles = ntiles;
+  // sample ranges: enough units to keep every SM busy with a small tail
+  int64_t range = 8192;
+  while (range > kStageK && ((ns + range - 1) / range) * ntiles < 8LL * sms) range /= 2;
+  P.range_len = range;
+  P.nunits = ((ns + range - 1) / range) * ntiles;
+  // stages of 64 samples between restarts of the tensor-memory accumulator (tuning knob)
+  static int flush = -1;
+  if (flush < 0) {
+    const char* env = getenv("BLM_TC_FLUSH_STAGES");
+    flush = env ? atoi(env) : 2;
+    if (flush < 1) flush = 1;
+  }
+  P.flush_stages = flush;
+  P.err = err;
+  const int grid = (int)(P.nunits < sms ? P.nunits : sms);
+  tc_accumulate_kernel<<<grid, kThreads, kSmemBytes, st>>>(P);
+  return cudaGetLastError();
+}
+
+}  // namespace blm

@@ -1,0 +1,84 @@
+"""Comparison norms for the CUDA path against the FP64 oracle (shared by the GPU tests)."""
+import numpy as np
+
+
+def matrix_err(S_got, S_ref, H_got=None, H_ref=None):
+    """Largest entry error in correlation scaling: |dS_xy| / sqrt(S_xx S_yy) and
+    |dH_xy| / (sqrt(S_xx S_yy) (1 + |H_00|)) (row/column 0 has S_00 = 1)."""
+    d = np.sqrt(np.abs(np.diag(S_ref)))
+    sc = np.outer(d, d)
+    es = np.max(np.abs(S_got - S_ref) / sc)
+    if H_got is None:
+        return es
+    eh = np.max(np.abs(H_got - H_ref) / (sc * (1.0 + abs(H_ref[0, 0]))))
+    return max(es, eh)
+
+
+def eig_err(l_got, l_ref):
+    l_got, l_ref = np.asarray(l_got), np.asarray(l_ref)
+    return np.max(np.abs(l_got - l_ref) / np.maximum(1.0, np.abs(l_ref)))
+
+
+def subspace_err(B_got, B_ref):
+    """1 - cos(largest principal angle) between the row spaces of B_got and B_ref."""
+    q1, _ = np.linalg.qr(np.asarray(B_got).T)
+    q2, _ = np.linalg.qr(np.asarray(B_ref).T)
+    s = np.linalg.svd(q1.T @ q2, compute_uv=False)
+    return 1.0 - s.min()
+
+
+def rel_err(x, ref):
+    return np.linalg.norm(np.asarray(x) - np.asarray(ref)) / max(np.linalg.norm(ref), 1e-300)
+
+
+def self_variation(oracle, O, G, E, w, offsets, n_keep, ref, **kw):
+    """Rounding sensitivity of the oracle itself: the same step on the reversed sample order.
+    Returns (|dE|, rel |d dmu|, max eigenvalue error, max subspace error)."""
+    wr = None if w is None else w[::-1]
+    r2 = oracle.blm_step(O[::-1], G[::-1], E[::-1], wr, offsets, n_keep, **kw)
+    de = abs(r2["e_pred"] - ref["e_pred"])
+    dd = rel_err(r2["dmu"], ref["dmu"])
+    dl = max(eig_err(a, b) for a, b in zip(r2["lam_b"], ref["lam_b"]))
+    ds = max(subspace_err(a, b) for a, b in zip(r2["B"], ref["B"]))
+    return de, dd, dl, ds
+
+
+def check_step(oracle, got, ref, O, G, E, w, offsets, n_keep, tol_mat, tol_e, tol_dmu, tol_eig,
+               tol_sub, shift=0.0, old_dirs=None, report=None, tol_own=None):
+    """Parity of one step.  Matrices element by element; eigen-solves against LAPACK on the GPU's
+    own matrices; the combined matrices against the oracle's second sweep run with the GPU's B;
+    E_pred and Delta mu against the independent oracle."""
+    import scipy.linalg
+    out = {}
+    nb = len(offsets) - 1
+    Bs = []
+    em = el = es = esv = 0.0
+    for b in range(nb):
+        S, H, lam, B = got["blocks"][b]
+        Bs.append(B)
+        em = max(em, matrix_err(S, ref["S_b"][b], H, ref["H_b"][b]))
+        el = max(el, eig_err(lam, ref["lam_b"][b]))
+        es = max(es, subspace_err(B, ref["B"][b]))
+        m_b = offsets[b + 1] - offsets[b]
+        lam_own, B_own, _ = oracle.block_solve(S, H, len(lam), m_b)
+        esv = max(esv, eig_err(lam, lam_own), subspace_err(B, B_own))
+        assert np.allclose(np.linalg.norm(B, axis=1), 1.0, atol=1e-12)
+    Sc_ref, Hc_ref = oracle.combined_matrices(O, G, E, w, offsets, Bs, shift=shift)
+    ec = matrix_err(got["S_c"], Sc_ref, got["H_c"], Hc_ref)
+    lam_c, _ = oracle.lowest_eigenpair(got["S_c"], got["H_c"])
+    out.update(block_matrix=em, block_eig=el, block_subspace=es, own_solver=esv, combined_matrix=ec,
+               combined_own_eig=abs(lam_c - got["e_pred"]), e_pred=abs(got["e_pred"] - ref["e_pred"]),
+               dmu=rel_err(got["dmu"], ref["dmu"]))
+    if report is not None:
+        report.update(out)
+    assert em < tol_mat, out
+    assert ec < tol_mat, out
+    tol_own = tol_eig if tol_own is None else tol_own
+    print("parity:", {k: float("%.3g" % v) for k, v in out.items()})
+    assert esv < tol_own, out
+    assert out["combined_own_eig"] < tol_own * max(1.0, abs(lam_c)), out
+    assert el < tol_eig, out
+    assert es < tol_sub, out
+    assert out["e_pred"] < tol_e, out
+    assert out["dmu"] < tol_dmu, out
+    return out

@@ -1,0 +1,188 @@
+"""GPU parity of the FP64 path (libblm.so through its C ABI) against the FP64 oracle.
+
+Element by element on the same seeded inputs: block matrices S_b, H_b, kept eigenvalues, the
+retained subspaces B^(b), the combined matrices, the predicted energy and the update.  Cases
+cover several tiles and ragged tails, uneven blocks, weights, an offset that stresses the
+centring, the diagonal shift, history directions (Eq. 9-10), chunked and host-memory input,
+the zero-variance limit and the out-of-order call errors.
+
+Tolerances (FP64 path): matrices 1e-10 in correlation scaling (block matrices against the
+oracle; combined matrices against the oracle's second sweep run with the GPU's B^(b)).  Eigen
+quantities carry the conditioning of S (10^6 - 10^8 here) on top of double rounding in both the
+oracle's QZ and the GPU's Cholesky + QR, so they are held to max(floor, 10 x the oracle's own
+change when the sample order is reversed): floors 1e-9 relative for eigenvalues (also against
+LAPACK on the GPU's own matrices), 1e-8 for retained subspaces (1 - cos of the largest principal
+angle), 1e-10 Hartree for E_pred, 1e-7 relative for Delta mu.
+"""
+import numpy as np
+import pytest
+
+import synth
+from synth import toy as T
+from oracle import blm_oracle
+from tests.parity import check_step, rel_err, self_variation
+
+pytestmark = pytest.mark.gpu
+
+TOL_MAT = 1e-10
+TOL_EIG = 1e-9
+TOL_SUB = 1e-8
+TOL_E = 1e-10
+TOL_DMU = 1e-7
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def run_gpu(torch, O, G, E, w, offsets, n_keep, chunks=None, shift=0.0, old_dirs=None,
+            host=False):
+    import paper_1702_01481_gb300 as blm
+    dev = torch.device("cuda:0")
+    if host:
+        tO, tG, tE = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (O, G, E))
+        tw = torch.from_numpy(w).pin_memory() if w is not None else None
+    else:
+        tO, tG, tE = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (O, G, E))
+        tw = torch.from_numpy(w).to(dev) if w is not None else None
+    n = O.shape[1]
+    n_old = 0 if old_dirs is None else old_dirs.shape[0]
+    D = torch.from_numpy(np.ascontiguousarray(old_dirs)).to(dev) if n_old else None
+    step = blm.Step(n, offsets, n_keep, n_old=n_old, old_dirs=D, shift=shift)
+    ns = O.shape[0]
+    chunks = chunks or [ns]
+    bounds = np.cumsum([0] + list(chunks))
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        step.accumulate(tO[a:b], tG[a:b], tE[a:b], tw[a:b] if tw is not None else None)
+    step.block_solve()
+    blocks = [step.block(b) for b in range(len(offsets) - 1)]
+    for a, b in reversed(list(zip(bounds[:-1], bounds[1:]))):
+        step.project(tO[a:b], tG[a:b], tE[a:b], tw[a:b] if tw is not None else None)
+    dmu = torch.empty(n, dtype=torch.float64, device=dev)
+    e = step.combined_solve(dmu)
+    Sc, Hc = step.combined()
+    step.close()
+    return dict(blocks=blocks, e_pred=e, dmu=dmu.cpu().numpy(), S_c=Sc, H_c=Hc)
+
+
+def compare(got, ref, O, G, E, w, offsets, n_keep, shift=0.0, old_dirs=None):
+    """FP64 parity; eigen quantities get max(floor, 10x the oracle's own sample-order
+    sensitivity) since both sides round differently through the conditioning of S."""
+    kw = dict(shift=shift, old_dirs=old_dirs)
+    de, dd, dl, ds = self_variation(blm_oracle, O, G, E, w, offsets, n_keep, ref, **kw)
+    return check_step(blm_oracle, got, ref, O, G, E, w, offsets, n_keep, tol_mat=TOL_MAT,
+                      tol_e=max(TOL_E, 10 * de), tol_dmu=max(TOL_DMU, 10 * dd),
+                      tol_eig=max(TOL_EIG, 10 * dl), tol_sub=max(TOL_SUB, 10 * ds),
+                      shift=shift, old_dirs=old_dirs)
+
+
+def test_n200_workload(torch_cuda):
+    wl = synth.workload("n200")
+    O, G, E = synth.samples(wl)
+    ref = blm_oracle.blm_step(O, G, E, None, wl.block_offsets, wl.n_keep)
+    got = run_gpu(torch_cuda, O, G, E, None, wl.block_offsets, wl.n_keep, chunks=[7001, 12999])
+    compare(got, ref, O, G, E, None, wl.block_offsets, wl.n_keep)
+
+
+def test_uneven_blocks_weights_offset_ragged(torch_cuda):
+    wl = synth.Workload("t", 150, 5003, [0, 37, 80, 81, 150], 4, decades=5.0, chunk=5003,
+                        offset=1.0, seed=7)
+    O, G, E = synth.samples(wl)
+    w = np.linspace(0.3, 1.7, O.shape[0])
+    ref = blm_oracle.blm_step(O, G, E, w, wl.block_offsets, wl.n_keep)
+    got = run_gpu(torch_cuda, O, G, E, w, wl.block_offsets, wl.n_keep, chunks=[1, 2047, 2955])
+    compare(got, ref, O, G, E, w, wl.block_offsets, wl.n_keep)
+
+
+def test_shift(torch_cuda):
+    wl = synth.Workload("t", 64, 4000, [0, 20, 44, 64], 3, decades=4.0, chunk=4000, seed=2)
+    O, G, E = synth.samples(wl)
+    ref = blm_oracle.blm_step(O, G, E, None, wl.block_offsets, wl.n_keep, shift=0.1)
+    got = run_gpu(torch_cuda, O, G, E, None, wl.block_offsets, wl.n_keep, shift=0.1)
+    compare(got, ref, O, G, E, None, wl.block_offsets, wl.n_keep, shift=0.1)
+
+
+def test_history_directions(torch_cuda):
+    wl = synth.Workload("t", 72, 3000, [0, 24, 48, 72], 2, decades=3.0, chunk=3000, seed=4)
+    O, G, E = synth.samples(wl)
+    rng = np.random.default_rng(1)
+    D = rng.normal(size=(2, 72)) * 0.1
+    ref = blm_oracle.blm_step(O, G, E, None, wl.block_offsets, wl.n_keep, old_dirs=D)
+    got = run_gpu(torch_cuda, O, G, E, None, wl.block_offsets, wl.n_keep, old_dirs=D)
+    compare(got, ref, O, G, E, None, wl.block_offsets, wl.n_keep, old_dirs=D)
+
+
+def test_host_memory_input_matches_device(torch_cuda):
+    wl = synth.Workload("t", 96, 3000, [0, 48, 96], 3, decades=4.0, chunk=3000, seed=5)
+    O, G, E = synth.samples(wl)
+    a = run_gpu(torch_cuda, O, G, E, None, wl.block_offsets, wl.n_keep)
+    b = run_gpu(torch_cuda, O, G, E, None, wl.block_offsets, wl.n_keep, host=True)
+    assert abs(a["e_pred"] - b["e_pred"]) < 1e-12
+    assert rel_err(b["dmu"], a["dmu"]) < 1e-10
+
+
+def test_zero_variance_toy(torch_cuda):
+    toy = T.make_toy()
+    O, G, E, w = T.sample(toy, np.zeros(toy.n), 3000)
+    got = run_gpu(torch_cuda, O, G, E, w, [0, 4, 8, 12], 4)
+    assert abs(got["e_pred"] - toy.e_ground) < 1e-9
+    assert np.max(np.abs(got["dmu"] - toy.a)) < 1e-8
+
+
+def test_n2048_full_parameter_count(torch_cuda):
+    """The 2048-parameter workload (16 blocks of 128, K = 10, overlap condition 1e8) at its full
+    parameter count and launch shape, on its first 20000 samples."""
+    wl = synth.workload("n2048")
+    O, G, E = synth.samples(wl, count=20000)
+    ref = blm_oracle.blm_step(O, G, E, None, wl.block_offsets, wl.n_keep)
+    got = run_gpu(torch_cuda, O, G, E, None, wl.block_offsets, wl.n_keep, chunks=[16384, 3616])
+    compare(got, ref, O, G, E, None, wl.block_offsets, wl.n_keep)
+
+
+def test_call_order_is_enforced(torch_cuda):
+    import paper_1702_01481_gb300 as blm
+    torch = torch_cuda
+    step = blm.Step(16, [0, 8, 16], 2)
+    O = torch.zeros(4, 16, dtype=torch.float64, device="cuda:0")
+    E = torch.zeros(4, dtype=torch.float64, device="cuda:0")
+    with pytest.raises(blm.BLMError) as e:
+        step.block_solve()
+    assert e.value.status == blm.BLM_ERR_STATE
+    with pytest.raises(blm.BLMError) as e:
+        step.project(O, O, E)
+    assert e.value.status == blm.BLM_ERR_STATE
+    dmu = torch.empty(16, dtype=torch.float64, device="cuda:0")
+    with pytest.raises(blm.BLMError) as e:
+        step.combined_solve(dmu)
+    assert e.value.status == blm.BLM_ERR_STATE
+    step.close()
+
+
+def test_singular_overlap_is_reported(torch_cuda):
+    import paper_1702_01481_gb300 as blm
+    torch = torch_cuda
+    ns, n = 64, 8
+    rng = np.random.default_rng(0)
+    O = rng.normal(size=(ns, n))
+    O[:, 3] = O[:, 2]                       # two identical derivative vectors: S singular
+    G = rng.normal(size=(ns, n))
+    E = rng.normal(size=ns)
+    dev = torch.device("cuda:0")
+    step = blm.Step(n, [0, 4, 8], 2)
+    step.accumulate(*(torch.from_numpy(a).to(dev) for a in (O, G, E)))
+    with pytest.raises(blm.BLMError) as e:
+        step.block_solve()
+    assert e.value.status == blm.BLM_ERR_NUMERIC
+    step.close()
+
+
+def test_empty_chunk_is_a_noop(torch_cuda):
+    wl = synth.Workload("t", 40, 800, [0, 20, 40], 2, decades=3.0, chunk=800, seed=9)
+    O, G, E = synth.samples(wl)
+    ref = blm_oracle.blm_step(O, G, E, None, wl.block_offsets, wl.n_keep)
+    got = run_gpu(torch_cuda, O, G, E, None, wl.block_offsets, wl.n_keep, chunks=[0, 800, 0])
+    compare(got, ref, O, G, E, None, wl.block_offsets, wl.n_keep)
