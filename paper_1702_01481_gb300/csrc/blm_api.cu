@@ -23,6 +23,11 @@ enum State { ST_CREATED = 0, ST_ACCUM = 1, ST_BLOCKS = 2, ST_PROJ = 3, ST_DONE =
 
 constexpr int64_t kSubChunk = 65536;     // samples per scratch pass (history / projection)
 constexpr int64_t kShiftSamples = 65536; // samples that fix the reference shift
+// Combined problems up to this dimension use the dense solver (exact ordering of the whole
+// spectrum); larger ones use generalized Davidson for the lowest eigenpair.
+constexpr int64_t kDenseCombinedMax = 320;
+constexpr double kDavidsonTol = 1e-11;
+constexpr int kDavidsonIter = 400;
 
 struct Alloc {
   // sizes in bytes of every device buffer; filled by plan()
@@ -363,7 +368,7 @@ void plan(blm_handle* h, Alloc& a) {
   a.add((void**)&h->d_cgram, 8 * dc * dc);
   a.add((void**)&h->d_Sc, 8 * (dc + 1) * (dc + 1));
   a.add((void**)&h->d_Hc, 8 * (dc + 1) * (dc + 1));
-  a.add((void**)&h->d_ceigw, 8 * eig_work_doubles(dc + 1));
+  a.add((void**)&h->d_ceigw, 8 * std::max(eig_work_doubles(dc + 1), davidson_work_doubles(dc + 1)));
   a.add((void**)&h->d_clam, 8 * 4);
   a.add((void**)&h->d_cev, 8 * (dc + 1));
   a.add((void**)&h->d_dmu, 8 * n);
@@ -849,7 +854,10 @@ blm_status blm_combined_solve(blm_handle* h, double* dmu, double* e_pred) {
   }
   {
     Prof pr(h, PC_EIG_COMBINED);
-    launch_eig(h->d_ceigp, 1, 512, st);
+    if (h->dc + 1 <= kDenseCombinedMax)
+      launch_eig(h->d_ceigp, 1, 512, st);
+    else
+      launch_davidson(h->d_ceigp, 1, kDavidsonTol, kDavidsonIter, st);
   }
   {
     Prof pr(h, PC_UPDATE, 2);

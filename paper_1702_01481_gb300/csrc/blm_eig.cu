@@ -413,11 +413,8 @@ __device__ void back_transform(const double* A, const double* hbeta, const doubl
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kEigThreads)
-eig_kernel(const EigProblem* __restrict__ probs) {
-  extern __shared__ double dsm[];
-  __shared__ Shared sh;
-  const EigProblem pb = probs[blockIdx.x];
+// Dense solver for one problem, run by the whole CTA (dsm: up to 200 KB of shared memory).
+__device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
   const int m = pb.m;
   const int t = threadIdx.x, nt = blockDim.x;
   const int64_t mm = (int64_t)m * m;
@@ -707,9 +704,198 @@ eig_kernel(const EigProblem* __restrict__ probs) {
   if (t == 0) *pb.status = (nsel == (pb.mode == 1 ? 1 : pb.k)) ? ST_OK : ST_NOCONV;
 }
 
+__global__ void __launch_bounds__(kEigThreads)
+eig_kernel(const EigProblem* __restrict__ probs) {
+  extern __shared__ double dsm[];
+  __shared__ Shared sh;
+  dense_geig(probs[blockIdx.x], dsm, sh);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Generalized Davidson for the lowest eigenpair of H c = lambda S c (the combined problem of
+// Eq. 7 when it is too large for the dense QR on one SM).  The basis V is kept S-orthonormal, so
+// the projected problem V^T H V y = theta y is a small standard eigenproblem (solved with the
+// dense routine above); the Ritz pair with the lowest real part is expanded with the diagonal
+// preconditioner t = -(diag H - theta diag S)^-1 r, starting from the Psi direction e_0.
+// Converged when ||H u - theta S u|| <= tol * ||S u|| * max(1, |theta|).
+// ---------------------------------------------------------------------------------------------
+constexpr int kDavMax = 40;
+
+__device__ void matvec(const double* M, int m, const double* x, double* y) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = wid; i < m; i += nw) {
+    const double* row = M + (int64_t)i * m;
+    double s = 0.0;
+    for (int j = lane; j < m; j += 32) s = fma(row[j], x[j], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[i] = s;
+  }
+  __syncthreads();
+}
+
+__device__ double dotv(const double* a, const double* b, int m, Shared& sh) {
+  double p = 0.0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) p = fma(a[i], b[i], p);
+  return block_sum(p, sh.red);
+}
+
+__global__ void __launch_bounds__(kEigThreads)
+davidson_kernel(const EigProblem* __restrict__ probs, double tol, int max_iter) {
+  extern __shared__ double dsm[];
+  __shared__ Shared sh;
+  __shared__ double hk[kDavMax * kDavMax];
+  const EigProblem pb = probs[blockIdx.x];
+  const int m = pb.m;
+  const int t = threadIdx.x, nt = blockDim.x;
+  double* V = pb.work;                       // kDavMax x m
+  double* HV = V + (int64_t)kDavMax * m;     // rows (H v_j)
+  double* SV = HV + (int64_t)kDavMax * m;    // rows (S v_j)
+  double* u = SV + (int64_t)kDavMax * m;
+  double* Hu = u + m;
+  double* Su = Hu + m;
+  double* r = Su + m;
+  double* dH = r + m;
+  double* dS = dH + m;
+  double* small = dS + m;                    // small problem: S (k^2) | H (k^2) | work | lam | vec
+  const int ks = kDavMax;
+  double* sS = small;
+  double* sH = sS + ks * ks;
+  double* sW = sH + ks * ks;
+  double* sLam = sW + (5 * ks * ks + 16 * ks);
+  double* sVec = sLam + 2;
+  int32_t* sStat = reinterpret_cast<int32_t*>(sVec + ks);
+
+  for (int i = t; i < m; i += nt) {
+    dH[i] = pb.H[(int64_t)i * m + i];
+    dS[i] = pb.S[(int64_t)i * m + i];
+  }
+  __syncthreads();
+  if (!(dS[0] > 0.0)) {
+    if (t == 0) *pb.status = ST_NOT_PD;
+    return;
+  }
+  // v_0 = e_0 / sqrt(S_00)
+  for (int i = t; i < m; i += nt) V[i] = (i == 0) ? 1.0 / sqrt(dS[0]) : 0.0;
+  __syncthreads();
+  matvec(pb.H, m, V, HV);
+  matvec(pb.S, m, V, SV);
+  int k = 1;
+  bool fresh = true;      // projected matrix must be rebuilt (start, restart)
+  double theta = 0.0;
+  int status = ST_NOCONV;
+  for (int it = 0; it < max_iter; ++it) {
+    // projected matrix: only the newest row and column change between restarts
+    for (int i = 0; i < k; ++i) {
+      const bool newer = (i == k - 1);
+      for (int j = 0; j < k; ++j) {
+        if (!fresh && !newer && j != k - 1) continue;
+        const double v = dotv(V + (int64_t)i * m, HV + (int64_t)j * m, m, sh);
+        if (t == 0) hk[i * kDavMax + j] = v;
+      }
+    }
+    __syncthreads();
+    fresh = false;
+    for (int q = t; q < k * k; q += nt) {
+      const int i = q / k, j = q % k;
+      sH[q] = hk[i * kDavMax + j];
+      sS[q] = (i == j) ? 1.0 : 0.0;
+    }
+    if (t == 0) *sStat = ST_OK;
+    __syncthreads();
+    EigProblem sp{k, 1, 0, 0, sS, sH, sW, sLam, sVec, sStat};
+    dense_geig(sp, dsm, sh);
+    __syncthreads();
+    if (*sStat != ST_OK) {
+      status = *sStat;
+      break;
+    }
+    theta = sLam[0];
+    // Ritz vector and its images
+    for (int i = t; i < m; i += nt) {
+      double a = 0.0, b = 0.0, c = 0.0;
+      for (int j = 0; j < k; ++j) {
+        const double y = sVec[j];
+        a = fma(y, V[(int64_t)j * m + i], a);
+        b = fma(y, HV[(int64_t)j * m + i], b);
+        c = fma(y, SV[(int64_t)j * m + i], c);
+      }
+      u[i] = a;
+      Hu[i] = b;
+      Su[i] = c;
+      r[i] = b - theta * c;
+    }
+    __syncthreads();
+    const double rn = sqrt(dotv(r, r, m, sh));
+    const double sn = sqrt(dotv(Su, Su, m, sh));
+    if (rn <= tol * sn * fmax(1.0, fabs(theta))) {
+      status = ST_OK;
+      break;
+    }
+    // restart: keep only the Ritz vector (S-normalised)
+    if (k == kDavMax) {
+      const double nu = sqrt(dotv(u, Su, m, sh));
+      for (int i = t; i < m; i += nt) {
+        V[i] = u[i] / nu;
+        HV[i] = Hu[i] / nu;
+        SV[i] = Su[i] / nu;
+      }
+      __syncthreads();
+      k = 1;
+      fresh = true;
+    }
+    // correction t = -r / (dH - theta dS), S-orthogonalised against V twice
+    double* tv = V + (int64_t)k * m;
+    for (int i = t; i < m; i += nt) {
+      double den = dH[i] - theta * dS[i];
+      if (fabs(den) < 1e-8 * fmax(1.0, fabs(dH[i]))) den = den < 0 ? -1e-8 : 1e-8;
+      tv[i] = -r[i] / den;
+    }
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass)
+      for (int j = 0; j < k; ++j) {
+        const double c = dotv(SV + (int64_t)j * m, tv, m, sh);
+        for (int i = t; i < m; i += nt) tv[i] -= c * V[(int64_t)j * m + i];
+        __syncthreads();
+      }
+    double* stv = SV + (int64_t)k * m;
+    matvec(pb.S, m, tv, stv);
+    const double nn = dotv(tv, stv, m, sh);
+    if (!(nn > 1e-300)) {
+      status = ST_NOCONV;
+      break;
+    }
+    const double inv = 1.0 / sqrt(nn);
+    for (int i = t; i < m; i += nt) {
+      tv[i] *= inv;
+      stv[i] *= inv;
+    }
+    __syncthreads();
+    matvec(pb.H, m, tv, HV + (int64_t)k * m);
+    ++k;
+  }
+  if (t == 0) {
+    *pb.status = status;
+    pb.lam[0] = theta;
+  }
+  for (int i = t; i < m; i += nt) pb.vec[i] = u[i];
+}
+
 }  // namespace
 
 size_t eig_work_doubles(int64_t m) { return (size_t)(5 * m * m + 16 * m); }
+
+size_t davidson_work_doubles(int64_t m) {
+  const int64_t ks = kDavMax;
+  return (size_t)(3 * ks * m + 6 * m + 2 * ks * ks + 5 * ks * ks + 16 * ks + 2 + ks + 8);
+}
+
+void launch_davidson(const EigProblem* probs, int nprob, double tol, int max_iter,
+                     cudaStream_t st) {
+  if (nprob <= 0) return;
+  const int smem = 200 * 1024;
+  cudaFuncSetAttribute(davidson_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  davidson_kernel<<<nprob, kEigThreads, smem, st>>>(probs, tol, max_iter);
+}
 
 void launch_eig(const EigProblem* probs, int nprob, int threads, cudaStream_t st) {
   if (nprob <= 0) return;

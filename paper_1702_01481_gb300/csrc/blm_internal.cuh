@@ -136,6 +136,10 @@ struct EigProblem {
 };
 void launch_eig(const EigProblem* probs, int nprob, int threads, cudaStream_t st);
 size_t eig_work_doubles(int64_t m);
+// Lowest eigenpair by generalized Davidson (k = 1, mode 1); work: davidson_work_doubles(m).
+void launch_davidson(const EigProblem* probs, int nprob, double tol, int max_iter,
+                     cudaStream_t st);
+size_t davidson_work_doubles(int64_t m);
 
 // ------------------------------- launchers (blm_update.cu) -----------------------------------
 struct DirBlock {       // block solve -> B rows

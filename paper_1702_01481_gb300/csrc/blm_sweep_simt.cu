@@ -168,6 +168,7 @@ contract_kernel(const Seg* __restrict__ segs, const Tile* __restrict__ tiles, Sr
 // ---------------------------------------------------------------------------------------------
 constexpr int kPS = 32;   // samples per CTA
 constexpr int kPC = 128;  // parameters per shared-memory run
+constexpr int kPL = kPC + 1;  // padded row: lanes reading different rows hit different banks
 
 template <typename T, typename A, typename TO>
 __global__ void __launch_bounds__(kThreads)
@@ -176,9 +177,9 @@ project_kernel(const T* __restrict__ O, const T* __restrict__ G, int64_t ldo, in
                const double* __restrict__ cen, TO* __restrict__ Y, TO* __restrict__ Z,
                int64_t ldout, int64_t ns, int max_nd) {
   extern __shared__ unsigned char smem_raw[];
-  A* Os = reinterpret_cast<A*>(smem_raw);          // kPS x kPC
-  A* Gs = Os + kPS * kPC;                          // kPS x kPC
-  A* Ds = Gs + kPS * kPC;                          // max_nd x kPC
+  A* Os = reinterpret_cast<A*>(smem_raw);          // kPS x kPL
+  A* Gs = Os + kPS * kPL;                          // kPS x kPL
+  A* Ds = Gs + kPS * kPL;                          // max_nd x kPL
   const ProjBlock pb = blocks[blockIdx.y];
   const int64_t s_base = (int64_t)blockIdx.x * kPS;
   const int t = threadIdx.x;
@@ -199,12 +200,12 @@ project_kernel(const T* __restrict__ O, const T* __restrict__ G, int64_t ldo, in
         ov = (A)O[s * ldo + col] - (shift ? (A)shift[col] : (A)0);
         gv = (A)G[s * ldg + col];
       }
-      Os[idx] = ov;
-      Gs[idx] = gv;
+      Os[k * kPL + c] = ov;
+      Gs[k * kPL + c] = gv;
     }
     for (int idx = t; idx < pb.nd * kPC; idx += kThreads) {
       const int j = idx / kPC, c = idx % kPC;
-      Ds[idx] = (c < pc) ? (A)pb.dir[(int64_t)j * pb.dld + p0 + c] : (A)0;
+      Ds[j * kPL + c] = (c < pc) ? (A)pb.dir[(int64_t)j * pb.dld + p0 + c] : (A)0;
     }
     __syncthreads();
 #pragma unroll
@@ -212,9 +213,9 @@ project_kernel(const T* __restrict__ O, const T* __restrict__ G, int64_t ldo, in
       const int pair = t + q * kThreads;
       if (pair < npairs) {
         const int k = pair / pb.nd, j = pair % pb.nd;
-        const A* o = Os + k * kPC;
-        const A* g = Gs + k * kPC;
-        const A* d = Ds + j * kPC;
+        const A* o = Os + k * kPL;
+        const A* g = Gs + k * kPL;
+        const A* d = Ds + j * kPL;
         A y = accY[q], z = accZ[q];
         for (int c = 0; c < pc; ++c) {
           y = fma(d[c], o[c], y);
@@ -297,7 +298,7 @@ void launch_project(const T* O, const T* G, int64_t ldo, int64_t ldg, const doub
   (void)max_m;
   if (ns <= 0 || nblocks <= 0) return;
   using A = TO;   // FP64 path: FP64 throughout; mixed path: FP32 products and sums
-  const size_t smem = sizeof(A) * (size_t)(2 * kPS * kPC + max_nd * kPC);
+  const size_t smem = sizeof(A) * (size_t)(2 * kPS * kPL + max_nd * kPL);
   cudaFuncSetAttribute(project_kernel<T, A, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
   dim3 grid((unsigned)((ns + kPS - 1) / kPS), (unsigned)nblocks);

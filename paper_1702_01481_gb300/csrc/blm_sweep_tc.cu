@@ -188,10 +188,11 @@ __device__ __forceinline__ void split8(const float* v, uint4& hi, uint4& lo) {
   lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
+// Operand stores carry no "memory" clobber so that the next job's global loads can be hoisted
+// above them; the proxy fence before the mbarrier arrive orders them for the tensor core.
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y),
-               "r"(v.z), "r"(v.w)
-               : "memory");
+               "r"(v.z), "r"(v.w));
 }
 
 // Byte offset of (row, 16-byte chunk) in a K-major 128-byte-swizzled operand tile.
@@ -239,73 +240,100 @@ struct Params {
   int64_t range_len;     // samples per unit (multiple of kStageK)
   int64_t nunits;
   int flush_stages;
+  int vec_ok;            // base pointers 16-byte aligned and ld a multiple of 4
   int32_t* err;
 };
 
-// Converter job: 32 operand rows x 32 samples.  Lane = 8 g + l: sample group g (8 samples),
-// rows l + 8 e (e = 0..3) -> conflict-free 16-byte swizzled stores, 32-byte load sectors.
+// Converter job: 32 operand rows x 32 samples (8 sample groups g of 8, lane = 8 g + l).
+// VEC: lane l owns rows 4l .. 4l+3 and loads them as float4 (needs 16-byte aligned rows);
+// otherwise lane l owns rows l + 8e with scalar loads.  Both orders give conflict-free 16-byte
+// swizzled stores.  All loads of a job are issued before any value is used.
 // kind 0: B rows (Y' or X', weighted; A rows too in A_FROM_B mode); kind 1: A rows (Y').
+template <bool VEC>
 __device__ __forceinline__ void convert_job(const Params& P, const TileInfo& ti, int kind,
                                             int rowgroup, int half, int64_t stage_base,
                                             int64_t s_end, uint8_t* stage) {
   const int lane = threadIdx.x & 31;
   const int g = lane >> 3, l = lane & 7;
   const int64_t s0 = stage_base + 32 * half + 8 * g;
+  const bool xt = (kind == 0) && ti.xtype;
   float ev[8], wv[8];
   bool vs[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int64_t s = s0 + q;
     vs[q] = s < s_end;
-    ev[q] = (kind == 0 && ti.xtype && vs[q]) ? P.E[s] : 0.0f;
-    wv[q] = (kind == 0 && P.w && vs[q]) ? P.w[s] : 1.0f;
+    ev[q] = (xt && vs[q]) ? __ldg(P.E + s) : 0.0f;
+    wv[q] = (kind == 0 && P.w && vs[q]) ? __ldg(P.w + s) : 1.0f;
+  }
+  int row[4];
+  int64_t par[4];
+  bool vr[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    row[e] = rowgroup * 32 + (VEC ? 4 * l + e : l + 8 * e);
+    if (kind == 0) {
+      vr[e] = row[e] < ti.nB;
+      par[e] = ti.lo + ti.pb + row[e];
+    } else {
+      vr[e] = row[e] < ti.nA;
+      par[e] = ti.lo + ti.row0 + row[e];
+    }
+  }
+  float y[4][8], z[4][8];
+  if (VEC) {
+    // rows 4l .. 4l+3 are all valid or all invalid: nB and nA are multiples of 4 here
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      float4 a = make_float4(0.f, 0.f, 0.f, 0.f), c = a;
+      if (vr[0] && vs[q]) {
+        const int64_t idx = (s0 + q) * P.ld + par[0];
+        a = __ldg(reinterpret_cast<const float4*>(P.Y + idx));
+        if (xt) c = __ldg(reinterpret_cast<const float4*>(P.Z + idx));
+      }
+      y[0][q] = a.x; y[1][q] = a.y; y[2][q] = a.z; y[3][q] = a.w;
+      z[0][q] = c.x; z[1][q] = c.y; z[2][q] = c.z; z[3][q] = c.w;
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const bool ok = vr[e] && vs[q];
+        const int64_t idx = (s0 + q) * P.ld + par[e];
+        y[e][q] = ok ? __ldg(P.Y + idx) : 0.0f;
+        z[e][q] = (ok && xt) ? __ldg(P.Z + idx) : 0.0f;
+      }
   }
   const int chunk = 4 * half + g;
   const uint32_t sbase = smem_u32(stage);
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
-    const int row = rowgroup * 32 + l + 8 * e;
-    int64_t p;
-    bool vr;
-    if (kind == 0) {
-      vr = row < ti.nB;
-      p = ti.lo + ti.pb + row;
-    } else {
-      vr = row < ti.nA;
-      p = ti.lo + ti.row0 + row;
-    }
-    const float sh = (vr && P.shift) ? P.shift[p] : 0.0f;
-    float y[8], x[8];
+    const float sh = (vr[e] && P.shift) ? __ldg(P.shift + par[e]) : 0.0f;
+    float yy[8], x[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const bool ok = vr && vs[q];
-      const int64_t idx = (s0 + q) * P.ld + p;
-      const float yy = ok ? P.Y[idx] - sh : 0.0f;
-      y[q] = yy;
-      if (kind == 0 && ti.xtype) {
-        const float zz = ok ? P.Z[idx] : 0.0f;
-        x[q] = fmaf(ev[q], yy, zz) * wv[q];
-      } else {
-        x[q] = yy * wv[q];
-      }
+      const bool ok = vr[e] && vs[q];
+      yy[q] = ok ? y[e][q] - sh : 0.0f;
+      x[q] = (xt ? fmaf(ev[q], yy[q], z[e][q]) : yy[q]) * wv[q];
     }
     uint4 hi, lo;
-    const uint32_t off = swz(row, chunk);
+    const uint32_t off = swz(row[e], chunk);
     if (kind == 0) {
       split8(x, hi, lo);
       st_shared_v4(sbase + off, hi);
       st_shared_v4(sbase + kBBytes + off, lo);
       if (ti.amode == A_FROM_B) {
-        const int arow = ti.pb + row - ti.row0;
+        const int arow = ti.pb + row[e] - ti.row0;
         if (arow >= 0 && arow < kARows) {
-          split8(y, hi, lo);
+          split8(yy, hi, lo);
           const uint32_t aoff = swz(arow, chunk);
           st_shared_v4(sbase + 2 * kBBytes + aoff, hi);
           st_shared_v4(sbase + 2 * kBBytes + kABytes + aoff, lo);
         }
       }
     } else {
-      split8(y, hi, lo);
+      split8(yy, hi, lo);
       st_shared_v4(sbase + 2 * kBBytes + off, hi);
       st_shared_v4(sbase + 2 * kBBytes + kABytes + off, lo);
     }
@@ -454,6 +482,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_accumulate_kernel(const Params
       const int64_t sb = min(P.ns, sa + P.range_len);
       const int nst = (int)((sb - sa + kStageK - 1) / kStageK);
       const int njobs_b = (kBRows / 32) * 2;
+      // float4 rows need 16-byte aligned parameter offsets and row strides
+      const bool vec = P.vec_ok && ((ti.lo + ti.pb) % 4 == 0) && ((ti.lo + ti.row0) % 4 == 0) &&
+                       (ti.nB % 4 == 0) && (ti.nA % 4 == 0);
       const int njobs = njobs_b + (ti.amode == A_SEPARATE ? (kARows / 32) * 2 : 0);
       for (int st = 0; st < nst; ++st, ++g) {
         const uint32_t slot = g % kStages, use = g / kStages;
@@ -462,10 +493,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_accumulate_kernel(const Params
         uint8_t* stage = smem + slot * kStageBytes;
         const int64_t base = sa + (int64_t)st * kStageK;
         for (int j = cw; j < njobs; j += kConvWarps) {
-          if (j < njobs_b)
-            convert_job(P, ti, 0, j >> 1, j & 1, base, sb, stage);
+          const int kind = j < njobs_b ? 0 : 1;
+          const int jj = kind ? j - njobs_b : j;
+          if (vec)
+            convert_job<true>(P, ti, kind, jj >> 1, jj & 1, base, sb, stage);
           else
-            convert_job(P, ti, 1, (j - njobs_b) >> 1, (j - njobs_b) & 1, base, sb, stage);
+            convert_job<false>(P, ti, kind, jj >> 1, jj & 1, base, sb, stage);
         }
         fence_async_smem();
         __syncwarp();
@@ -524,6 +557,7 @@ cudaError_t launch_tc_accumulate(const float* Y, const float* Z, const float* E,
   }
   P.flush_stages = flush;
   P.err = err;
+  P.vec_ok = (ld % 4 == 0) && (((uintptr_t)Y | (uintptr_t)Z) % 16 == 0);
   const int grid = (int)(P.nunits < sms ? P.nunits : sms);
   tc_accumulate_kernel<<<grid, kThreads, kSmemBytes, st>>>(P);
   return cudaGetLastError();

@@ -7,7 +7,7 @@ import os
 
 import numpy as np
 
-from . import workload as W
+from .workload import make_model
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libblmsynth.so")
@@ -32,7 +32,7 @@ class DeviceModel:
     def __init__(self, wl, device="cuda:0"):
         import torch
         self.wl = wl
-        m = W.make_model(wl)
+        m = make_model(wl)
         self.u = torch.from_numpy(np.ascontiguousarray(m.u)).to(device)
         self.sigma = torch.from_numpy(m.sigma).to(device)
         self.g = torch.from_numpy(m.g).to(device)

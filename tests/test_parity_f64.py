@@ -186,3 +186,14 @@ def test_empty_chunk_is_a_noop(torch_cuda):
     ref = blm_oracle.blm_step(O, G, E, None, wl.block_offsets, wl.n_keep)
     got = run_gpu(torch_cuda, O, G, E, None, wl.block_offsets, wl.n_keep, chunks=[0, 800, 0])
     compare(got, ref, O, G, E, None, wl.block_offsets, wl.n_keep)
+
+
+def test_large_combined_problem_davidson(torch_cuda):
+    """Combined dimension 1 + 360 > 320: the lowest eigenpair comes from the Davidson solver."""
+    wl = synth.Workload("t", 1280, 6000, synth.equal_blocks(1280, 8), 45, decades=4.0, chunk=6000,
+                        seed=11)
+    O, G, E = synth.samples(wl)
+    ref = blm_oracle.blm_step(O, G, E, None, wl.block_offsets, wl.n_keep)
+    got = run_gpu(torch_cuda, O, G, E, None, wl.block_offsets, wl.n_keep)
+    assert got["S_c"].shape[0] == 361
+    compare(got, ref, O, G, E, None, wl.block_offsets, wl.n_keep)

@@ -5,12 +5,21 @@ measures only the path's arithmetic: operands split into bf16 hi + lo (four prod
 product is exact to ~2^-16 relative and unbiased), FP32 tensor-memory accumulation restarted every
 128 samples, FP64 centring and FP64 solves.
 
-Tolerances: S_b, H_b and the combined matrices (the latter against the oracle's second sweep run
-with the GPU's B^(b)) 1e-6 in correlation scaling (|dA_xy| / sqrt(S_xx S_yy)); E_pred 1e-8
-Hartree; Delta mu 1e-4 relative.  Kept eigenvalues (1e-5 relative) and retained subspaces (1e-4)
-carry the matrix error times the conditioning of the block problem, so they are looser; the FP64
-eigen-solves themselves are held to max(1e-9, 10 x the oracle's sample-order sensitivity)
-against LAPACK on the GPU's own matrices.
+Error model.  hi + lo represents each FP32 operand v to |v - hi - lo| <= 2^-16 |v| with a
+zero-mean residual (RMS ~ 6e-6 relative); each product carries two such residuals, independent
+from sample to sample, so their contribution to a sum over N samples falls as 1/sqrt(N): RMS
+~ 2 * 6e-6 * sqrt(3 / N) of the correlation-scaled entry, and the largest of ~10^5 - 10^6 entries
+sits ~ 4.5 RMS out.  (Restarting the FP32 tensor-memory accumulator every 64, 128 or 256 samples
+gives the same errors to three digits: accumulation is not the limit.)  The targets hold at the
+size of the step they are stated for, N = 10^6 samples; for a test sample of N the tolerances are
+the targets widened by sqrt(10^6 / N):
+  S_b, H_b and the combined matrices (the latter against the oracle's second sweep run with the
+  GPU's B^(b)): 1e-6 in correlation scaling (|dA_xy| / sqrt(S_xx S_yy));
+  E_pred: 1e-8 Hartree;  Delta mu: 1e-4 relative;
+  kept eigenvalues 1e-5 relative and retained subspaces 1e-4 (matrix error times the
+  conditioning of the block problem).
+The FP64 eigen-solves themselves are held to max(1e-9, 10 x the oracle's sample-order
+sensitivity) against LAPACK on the GPU's own matrices.
 """
 import numpy as np
 import pytest
@@ -65,12 +74,13 @@ def f32_inputs(wl, count=None):
 
 
 def check(got, ref, O, G, E, w, offsets, n_keep):
+    scale = max(1.0, np.sqrt(1.0e6 / O.shape[0]))
     O, G, E = (a.astype(np.float64) for a in (O, G, E))
     w = None if w is None else np.asarray(w, np.float32).astype(np.float64)
     de, dd, dl, ds = self_variation(blm_oracle, O, G, E, w, offsets, n_keep, ref)
-    return check_step(blm_oracle, got, ref, O, G, E, w, offsets, n_keep, tol_mat=TOL_MAT,
-                      tol_e=TOL_E, tol_dmu=TOL_DMU, tol_eig=TOL_EIG, tol_sub=TOL_SUB,
-                      tol_own=max(1e-9, 10 * dl, 10 * ds))
+    return check_step(blm_oracle, got, ref, O, G, E, w, offsets, n_keep, tol_mat=TOL_MAT * scale,
+                      tol_e=TOL_E * scale, tol_dmu=TOL_DMU * scale, tol_eig=TOL_EIG * scale,
+                      tol_sub=TOL_SUB * scale, tol_own=max(1e-9, 10 * dl, 10 * ds))
 
 
 def oracle_f32(O, G, E, w, offsets, n_keep):
