@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(_HERE, "libblm.so")
 
 BLM_OK, BLM_ERR_ARG, BLM_ERR_STATE, BLM_ERR_NUMERIC, BLM_ERR_NOMEM, BLM_ERR_CUDA, \
     BLM_ERR_TIMEOUT, BLM_ERR_UNSUPPORTED = range(8)
-BLM_PREC_F64, BLM_PREC_BF16X4 = 0, 1
+BLM_PREC_F64, BLM_PREC_BF16X4, BLM_PREC_TF32X3 = 0, 1, 2
 BLM_IN_F64, BLM_IN_F32 = 0, 1
 STATUS_NAMES = {0: "BLM_OK", 1: "BLM_ERR_ARG", 2: "BLM_ERR_STATE", 3: "BLM_ERR_NUMERIC",
                 4: "BLM_ERR_NOMEM", 5: "BLM_ERR_CUDA", 6: "BLM_ERR_TIMEOUT", 7: "BLM_ERR_UNSUPPORTED"}

@@ -205,7 +205,8 @@ blm_status validate(const blm_problem* p, std::string& why) {
   if (p->n_old < 0 || p->n_old > 16) { why = "n_old must be in 0..16"; return BLM_ERR_ARG; }
   if (p->n_old > 0 && !p->old_dirs) { why = "old_dirs is NULL"; return BLM_ERR_ARG; }
   if (p->n_old > 0 && p->n_blocks < 2) { why = "history directions need >= 2 blocks"; return BLM_ERR_ARG; }
-  if (p->precision != BLM_PREC_F64 && p->precision != BLM_PREC_BF16X4) {
+  if (p->precision != BLM_PREC_F64 && p->precision != BLM_PREC_BF16X4 &&
+      p->precision != BLM_PREC_TF32X3) {
     why = "unknown precision";
     return BLM_ERR_ARG;
   }
@@ -213,11 +214,11 @@ blm_status validate(const blm_problem* p, std::string& why) {
     why = "unknown input_type";
     return BLM_ERR_ARG;
   }
-  if (p->precision == BLM_PREC_BF16X4 && p->input_type != BLM_IN_F32) {
-    why = "the split-BF16 path takes FP32 inputs";
+  if (p->precision != BLM_PREC_F64 && p->input_type != BLM_IN_F32) {
+    why = "the split-precision tensor-core paths take FP32 inputs";
     return BLM_ERR_UNSUPPORTED;
   }
-  if (p->precision == BLM_PREC_BF16X4 && p->n_old > 0) {
+  if (p->precision != BLM_PREC_F64 && p->n_old > 0) {
     why = "history directions run on the FP64 path only";
     return BLM_ERR_UNSUPPORTED;
   }
@@ -427,7 +428,7 @@ blm_status accumulate_dev(blm_handle* h, const T* O, const T* G, const T* E, con
         h->d_colsum, h->n, (double)cnt, h->in_type == BLM_IN_F32, h->d_shift, h->d_shift32);
     h->shift_set = true;
   }
-  const bool mixed = h->prec == BLM_PREC_BF16X4;
+  const bool mixed = h->prec != BLM_PREC_F64;
   {
     Prof pr(h, PC_SUMS);
     launch_sums<T>(O, G, E, w, ns, ld, ld, h->n, h->d_shift, h->d_vec, h->d_vec + h->n,
@@ -467,7 +468,8 @@ blm_status accumulate_dev(blm_handle* h, const T* O, const T* G, const T* E, con
     Prof pr(h, PC_TC1);
     cudaError_t e = launch_tc_accumulate((const float*)O, (const float*)G, (const float*)E,
                                          (const float*)w, ns, ld, h->d_shift32, h->d_tc1,
-                                         h->ntc1, h->d_status + h->nb + 2, st);
+                                         h->ntc1, h->d_status + h->nb + 2,
+                                         h->prec == BLM_PREC_TF32X3, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "launch_tc_accumulate");
   }
   return BLM_OK;
@@ -511,7 +513,8 @@ blm_status project_dev(blm_handle* h, const T* O, const T* G, const T* E, const 
       }
       Prof pr(h, PC_TC2);
       cudaError_t e = launch_tc_accumulate(PY, PZ, Es, ws, cnt, dc, nullptr, h->d_tc2, h->ntc2,
-                                           h->d_status + h->nb + 2, st);
+                                           h->d_status + h->nb + 2, h->prec == BLM_PREC_TF32X3,
+                                           st);
       if (e != cudaSuccess) return cuda_fail(h, e, "launch_tc_accumulate (combined)");
     }
   }
@@ -723,7 +726,7 @@ blm_status blm_create(const blm_problem* p, void* stream, blm_handle** out) {
     if (s == BLM_OK) s = upload(h, dbk, &h->d_dirb);
     if (s == BLM_OK) s = upload(h, cp, &h->d_ceigp);
   }
-  if (s == BLM_OK && h->prec == BLM_PREC_BF16X4) {
+  if (s == BLM_OK && h->prec != BLM_PREC_F64) {
     // tensor-core tiles: 128 rows x 256 columns of [Y'Y'^T | Y'(E Y' + Z)^T] per block, and the
     // same over the combined directions (one block of dc columns of the projection scratch)
     std::vector<TcTile> t1, t2;

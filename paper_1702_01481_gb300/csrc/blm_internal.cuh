@@ -91,7 +91,8 @@ struct TcTile {
 bool tc_supported();
 cudaError_t launch_tc_accumulate(const float* Y, const float* Z, const float* E, const float* w,
                                  int64_t ns, int64_t ld, const float* shift32,
-                                 const TcTile* tiles, int ntiles, int32_t* err, cudaStream_t st);
+                                 const TcTile* tiles, int ntiles, int32_t* err, int tf32,
+                                 cudaStream_t st);
 
 // ------------------------------- launchers (blm_assemble.cu) ---------------------------------
 struct BlockAsm {

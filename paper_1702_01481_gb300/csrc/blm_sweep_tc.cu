@@ -33,7 +33,10 @@ namespace {
 
 constexpr int kWarps = 16;
 constexpr int kThreads = kWarps * 32;
-constexpr int kStageK = 64;                       // samples per stage
+constexpr int kStageK = 64;                       // samples per stage (BF16 operands)
+constexpr int kStageKTf = 32;                     // samples per stage (TF32 operands)
+template <bool TF>
+__device__ __host__ constexpr int stage_k() { return TF ? kStageKTf : kStageK; }
 constexpr int kStages = 2;
 constexpr int kBRows = 256;
 constexpr int kARows = 128;
@@ -129,6 +132,19 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
       : "memory");
 }
 
+// Instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major, M = 128, N = 256.
+constexpr uint32_t kIdescTf = (1u << 4) | (2u << 7) | (2u << 10) | ((256u >> 3) << 17) |
+                              ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdescTf), "r"(acc)
+      : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -190,6 +206,23 @@ __device__ __forceinline__ void split8(const float* v, uint4& hi, uint4& lo) {
 
 // Operand stores carry no "memory" clobber so that the next job's global loads can be hoisted
 // above them; the proxy fence before the mbarrier arrive orders them for the tensor core.
+// Split 8 values into TF32 hi (round to nearest) and FP32 lo = v - hi (exact); the tensor core
+// reads lo's top 19 bits, so hi + lo represents v to 2^-22 relative.  Two 16-byte chunks each.
+__device__ __forceinline__ void split8_tf32(const float* v, uint4* hi, uint4* lo) {
+  uint32_t h[8], l[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    uint32_t t;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(v[k]));
+    h[k] = t;
+    l[k] = __float_as_uint(v[k] - __uint_as_float(t));
+  }
+  hi[0] = make_uint4(h[0], h[1], h[2], h[3]);
+  hi[1] = make_uint4(h[4], h[5], h[6], h[7]);
+  lo[0] = make_uint4(l[0], l[1], l[2], l[3]);
+  lo[1] = make_uint4(l[4], l[5], l[6], l[7]);
+}
+
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y),
                "r"(v.z), "r"(v.w));
@@ -249,7 +282,7 @@ struct Params {
 // otherwise lane l owns rows l + 8e with scalar loads.  Both orders give conflict-free 16-byte
 // swizzled stores.  All loads of a job are issued before any value is used.
 // kind 0: B rows (Y' or X', weighted; A rows too in A_FROM_B mode); kind 1: A rows (Y').
-template <bool VEC>
+template <bool VEC, bool TF>
 __device__ __forceinline__ void convert_job(const Params& P, const TileInfo& ti, int kind,
                                             int rowgroup, int half, int64_t stage_base,
                                             int64_t s_end, uint8_t* stage) {
@@ -305,7 +338,8 @@ __device__ __forceinline__ void convert_job(const Params& P, const TileInfo& ti,
         z[e][q] = (ok && xt) ? __ldg(P.Z + idx) : 0.0f;
       }
   }
-  const int chunk = 4 * half + g;
+  // BF16: one 16-byte chunk of 8 samples per row; TF32: two chunks of 4 samples
+  const int chunk = TF ? 2 * g : 4 * half + g;
   const uint32_t sbase = smem_u32(stage);
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
@@ -317,29 +351,45 @@ __device__ __forceinline__ void convert_job(const Params& P, const TileInfo& ti,
       yy[q] = ok ? y[e][q] - sh : 0.0f;
       x[q] = (xt ? fmaf(ev[q], yy[q], z[e][q]) : yy[q]) * wv[q];
     }
-    uint4 hi, lo;
     const uint32_t off = swz(row[e], chunk);
-    if (kind == 0) {
-      split8(x, hi, lo);
-      st_shared_v4(sbase + off, hi);
-      st_shared_v4(sbase + kBBytes + off, lo);
-      if (ti.amode == A_FROM_B) {
-        const int arow = ti.pb + row[e] - ti.row0;
-        if (arow >= 0 && arow < kARows) {
-          split8(yy, hi, lo);
-          const uint32_t aoff = swz(arow, chunk);
-          st_shared_v4(sbase + 2 * kBBytes + aoff, hi);
-          st_shared_v4(sbase + 2 * kBBytes + kABytes + aoff, lo);
-        }
+    const int arow = ti.pb + row[e] - ti.row0;
+    const bool a_from_b = (kind == 0) && (ti.amode == A_FROM_B) && arow >= 0 && arow < kARows;
+    const uint32_t aoff = swz(kind == 0 ? arow : row[e], chunk);
+    if (TF) {
+      uint4 hi[2], lo[2];
+      const uint32_t off1 = swz(row[e], chunk + 1);
+      if (kind == 0) {
+        split8_tf32(x, hi, lo);
+        st_shared_v4(sbase + off, hi[0]);
+        st_shared_v4(sbase + off1, hi[1]);
+        st_shared_v4(sbase + kBBytes + off, lo[0]);
+        st_shared_v4(sbase + kBBytes + off1, lo[1]);
+      }
+      if (kind == 1 || a_from_b) {
+        split8_tf32(yy, hi, lo);
+        const uint32_t aoff1 = swz(kind == 0 ? arow : row[e], chunk + 1);
+        st_shared_v4(sbase + 2 * kBBytes + aoff, hi[0]);
+        st_shared_v4(sbase + 2 * kBBytes + aoff1, hi[1]);
+        st_shared_v4(sbase + 2 * kBBytes + kABytes + aoff, lo[0]);
+        st_shared_v4(sbase + 2 * kBBytes + kABytes + aoff1, lo[1]);
       }
     } else {
-      split8(yy, hi, lo);
-      st_shared_v4(sbase + 2 * kBBytes + off, hi);
-      st_shared_v4(sbase + 2 * kBBytes + kABytes + off, lo);
+      uint4 hi, lo;
+      if (kind == 0) {
+        split8(x, hi, lo);
+        st_shared_v4(sbase + off, hi);
+        st_shared_v4(sbase + kBBytes + off, lo);
+      }
+      if (kind == 1 || a_from_b) {
+        split8(yy, hi, lo);
+        st_shared_v4(sbase + 2 * kBBytes + aoff, hi);
+        st_shared_v4(sbase + 2 * kBBytes + kABytes + aoff, lo);
+      }
     }
   }
 }
 
+template <bool TF>
 __global__ void __launch_bounds__(kThreads, 1) tc_accumulate_kernel(const Params P) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -378,7 +428,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_accumulate_kernel(const Params
       const TileInfo ti = decode_tile(P.tiles[u % P.ntiles], P.w != nullptr);
       const int64_t sa = (u / P.ntiles) * P.range_len;
       const int64_t sb = min(P.ns, sa + P.range_len);
-      const int nst = (int)((sb - sa + kStageK - 1) / kStageK);
+      const int nst = (int)((sb - sa + stage_k<TF>() - 1) / stage_k<TF>());
       for (int st = 0; st < nst && alive; ++st, ++g) {
         const uint32_t slot = g % kStages, use = g / kStages;
         uint32_t acc = 1;
@@ -401,13 +451,20 @@ __global__ void __launch_bounds__(kThreads, 1) tc_accumulate_kernel(const Params
             ah = bh + 2 * kBBytes;
             al = ah + kABytes;
           }
+          // four K-steps of 32 bytes per 128-byte operand row
 #pragma unroll
-          for (int ks = 0; ks < kStageK / 16; ++ks) {
+          for (int ks = 0; ks < 4; ++ks) {
             const uint32_t o = ks * 32;
-            mma_bf16(tmem, sdesc(ah + o), sdesc(bh + o), acc);
-            mma_bf16(tmem, sdesc(ah + o), sdesc(bl + o), 1);
-            mma_bf16(tmem, sdesc(al + o), sdesc(bh + o), 1);
-            mma_bf16(tmem, sdesc(al + o), sdesc(bl + o), 1);
+            if (TF) {
+              mma_tf32(tmem, sdesc(ah + o), sdesc(bh + o), acc);
+              mma_tf32(tmem, sdesc(ah + o), sdesc(bl + o), 1);
+              mma_tf32(tmem, sdesc(al + o), sdesc(bh + o), 1);
+            } else {
+              mma_bf16(tmem, sdesc(ah + o), sdesc(bh + o), acc);
+              mma_bf16(tmem, sdesc(ah + o), sdesc(bl + o), 1);
+              mma_bf16(tmem, sdesc(al + o), sdesc(bh + o), 1);
+              mma_bf16(tmem, sdesc(al + o), sdesc(bl + o), 1);
+            }
             acc = 1;
           }
           mma_commit(&bars->op_empty[slot]);
@@ -432,7 +489,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_accumulate_kernel(const Params
       const TileInfo ti = decode_tile(P.tiles[u % P.ntiles], P.w != nullptr);
       const int64_t sa = (u / P.ntiles) * P.range_len;
       const int64_t sb = min(P.ns, sa + P.range_len);
-      const int nst = (int)((sb - sa + kStageK - 1) / kStageK);
+      const int nst = (int)((sb - sa + stage_k<TF>() - 1) / stage_k<TF>());
       const int nint = (nst + fs - 1) / fs;
       for (int it = 0; it < nint; ++it, ++k) {
         alive = mbar_wait(&bars->l1_full, k & 1, bars, P.err, 13);
@@ -480,25 +537,27 @@ __global__ void __launch_bounds__(kThreads, 1) tc_accumulate_kernel(const Params
       const TileInfo ti = decode_tile(P.tiles[u % P.ntiles], P.w != nullptr);
       const int64_t sa = (u / P.ntiles) * P.range_len;
       const int64_t sb = min(P.ns, sa + P.range_len);
-      const int nst = (int)((sb - sa + kStageK - 1) / kStageK);
-      const int njobs_b = (kBRows / 32) * 2;
+      const int nst = (int)((sb - sa + stage_k<TF>() - 1) / stage_k<TF>());
+      const int halves = TF ? 1 : 2;               // 32-sample halves per stage
+      const int njobs_b = (kBRows / 32) * halves;
       // float4 rows need 16-byte aligned parameter offsets and row strides
       const bool vec = P.vec_ok && ((ti.lo + ti.pb) % 4 == 0) && ((ti.lo + ti.row0) % 4 == 0) &&
                        (ti.nB % 4 == 0) && (ti.nA % 4 == 0);
-      const int njobs = njobs_b + (ti.amode == A_SEPARATE ? (kARows / 32) * 2 : 0);
+      const int njobs = njobs_b + (ti.amode == A_SEPARATE ? (kARows / 32) * halves : 0);
       for (int st = 0; st < nst; ++st, ++g) {
         const uint32_t slot = g % kStages, use = g / kStages;
         alive = mbar_wait(&bars->op_empty[slot], (use & 1) ^ 1, bars, P.err, 14);
         if (!alive) break;
         uint8_t* stage = smem + slot * kStageBytes;
-        const int64_t base = sa + (int64_t)st * kStageK;
+        const int64_t base = sa + (int64_t)st * stage_k<TF>();
         for (int j = cw; j < njobs; j += kConvWarps) {
           const int kind = j < njobs_b ? 0 : 1;
           const int jj = kind ? j - njobs_b : j;
+          const int rg = TF ? jj : jj >> 1, hf = TF ? 0 : (jj & 1);
           if (vec)
-            convert_job<true>(P, ti, kind, jj >> 1, jj & 1, base, sb, stage);
+            convert_job<true, TF>(P, ti, kind, rg, hf, base, sb, stage);
           else
-            convert_job<false>(P, ti, kind, jj >> 1, jj & 1, base, sb, stage);
+            convert_job<false, TF>(P, ti, kind, rg, hf, base, sb, stage);
         }
         fence_async_smem();
         __syncwarp();
@@ -522,7 +581,7 @@ bool tc_supported() { return true; }
 
 cudaError_t launch_tc_accumulate(const float* Y, const float* Z, const float* E, const float* w,
                                  int64_t ns, int64_t ld, const float* shift32,
-                                 const TcTile* tiles, int ntiles, int32_t* err,
+                                 const TcTile* tiles, int ntiles, int32_t* err, int tf32,
                                  cudaStream_t st) {
   if (ns <= 0 || ntiles <= 0) return cudaSuccess;
   static int sms = 0;
@@ -530,7 +589,9 @@ cudaError_t launch_tc_accumulate(const float* Y, const float* Z, const float* E,
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(tc_accumulate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(tc_accumulate_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kSmemBytes);
+    cudaFuncSetAttribute(tc_accumulate_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          kSmemBytes);
   }
   Params P;
@@ -545,21 +606,25 @@ cudaError_t launch_tc_accumulate(const float* Y, const float* Z, const float* E,
   P.ntiles = ntiles;
   // sample ranges: enough units to keep every SM busy with a small tail
   int64_t range = 8192;
-  while (range > kStageK && ((ns + range - 1) / range) * ntiles < 8LL * sms) range /= 2;
+  const int64_t sk = tf32 ? kStageKTf : kStageK;
+  while (range > sk && ((ns + range - 1) / range) * ntiles < 8LL * sms) range /= 2;
   P.range_len = range;
   P.nunits = ((ns + range - 1) / range) * ntiles;
-  // stages of 64 samples between restarts of the tensor-memory accumulator (tuning knob)
+  // stages between restarts of the tensor-memory accumulator: 128 samples
   static int flush = -1;
   if (flush < 0) {
-    const char* env = getenv("BLM_TC_FLUSH_STAGES");
-    flush = env ? atoi(env) : 2;
-    if (flush < 1) flush = 1;
+    const char* env = getenv("BLM_TC_FLUSH_SAMPLES");
+    flush = env ? atoi(env) : 128;
+    if (flush < 32) flush = 32;
   }
-  P.flush_stages = flush;
+  P.flush_stages = (int)(flush / sk) > 0 ? (int)(flush / sk) : 1;
   P.err = err;
   P.vec_ok = (ld % 4 == 0) && (((uintptr_t)Y | (uintptr_t)Z) % 16 == 0);
   const int grid = (int)(P.nunits < sms ? P.nunits : sms);
-  tc_accumulate_kernel<<<grid, kThreads, kSmemBytes, st>>>(P);
+  if (tf32)
+    tc_accumulate_kernel<true><<<grid, kThreads, kSmemBytes, st>>>(P);
+  else
+    tc_accumulate_kernel<false><<<grid, kThreads, kSmemBytes, st>>>(P);
   return cudaGetLastError();
 }
 
