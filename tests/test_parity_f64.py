@@ -199,9 +199,9 @@ def test_large_combined_problem_davidson(torch_cuda):
     compare(got, ref, O, G, E, None, wl.block_offsets, wl.n_keep)
 
 
-def test_blocks_of_256_locate_then_refine(torch_cuda):
-    """Blocks of 256 (problem dimension 257): the block solver locates eigenvalues with an FP32
-    QR in shared memory and refines them in FP64; FP64 parity must be unaffected."""
+def test_blocks_of_256_windowed_qr(torch_cuda):
+    """Blocks of 256 (problem dimension 257): the QR sweeps span several shared-memory windows
+    and the off-window row and column operations run from the stored reflectors."""
     wl = synth.Workload("t", 768, 6000, synth.equal_blocks(768, 3), 20, decades=6.0, chunk=6000,
                         seed=12, noise="student3")
     O, G, E = synth.samples(wl)
