@@ -68,6 +68,8 @@ struct blm_handle {
   // device buffers
   double* d_shift = nullptr;
   float* d_shift32 = nullptr;
+  float* d_B32 = nullptr;                   // B^(b) rows in FP32 (mixed-path projection)
+  int64_t B_words = 0;                      // doubles in d_B
   double* d_colsum = nullptr;
   double* d_vec = nullptr;       // sO | sEO | sG  (3n)
   double* d_scal = nullptr;      // [sw, sE, count, alpha]
@@ -337,6 +339,7 @@ void plan(blm_handle* h, Alloc& a) {
   const int64_t EWsz = h->eigw_off.back() + (int64_t)eig_work_doubles(h->db.back() + 1);
   const int64_t VOsz = h->vec_off.back() + (int64_t)h->Kb.back() * (h->db.back() + 1);
   const int64_t BOsz = h->B_off.back() + (int64_t)h->Kb.back() * h->Mb.back();
+  h->B_words = BOsz;
   const int64_t LOsz = h->lam_off.back() + h->Kb.back();
   const int64_t dc = h->dc, R = h->R;
   const int64_t scr_cols = std::max<int64_t>(dc, R);
@@ -362,6 +365,7 @@ void plan(blm_handle* h, Alloc& a) {
   a.add((void**)&h->d_lam, 8 * LOsz);
   a.add((void**)&h->d_evec, 8 * VOsz);
   a.add((void**)&h->d_B, 8 * BOsz);
+  a.add((void**)&h->d_B32, 4 * BOsz);
   a.add((void**)&h->d_status, 4 * (h->nb + 8));
   a.add((void**)&h->d_Cc, 8 * dc * 2 * dc);
   a.add((void**)&h->d_cvec, 8 * 3 * dc);
@@ -454,7 +458,7 @@ blm_status accumulate_dev(blm_handle* h, const T* O, const T* G, const T* E, con
         const T* ws = w ? w + s0 : nullptr;
         // t_jk = O'_k . D_jk and u_jk = G_k . D_jk (Eq. 9 ratios) for every block k
         Prof pr(h, PC_HIST, 3);
-        launch_project<double, double>(Os, Gs, ld, ld, h->d_shift, h->d_pbD, h->nb, nullptr, TY,
+        launch_project<double, double>(Os, Gs, ld, ld, h->d_shift, nullptr, h->d_pbD, h->nb, nullptr, TY,
                                        TZ, R, cnt, h->maxM, h->n_old, st);
         launch_sums<double>(TY, TZ, Es, ws, cnt, R, R, R, nullptr, h->d_hvec, h->d_hvec + R,
                             h->d_hvec + 2 * R, nullptr, false, st);
@@ -492,7 +496,7 @@ blm_status project_dev(blm_handle* h, const T* O, const T* G, const T* E, const 
       double* PZ = (double*)h->d_scrZ;
       {
         Prof pr(h, PC_PROJECT, 2);
-        launch_project<double, double>(Os, Gs, ld, ld, h->d_shift, h->d_pbB, h->nb, h->d_cen, PY,
+        launch_project<double, double>(Os, Gs, ld, ld, h->d_shift, nullptr, h->d_pbB, h->nb, h->d_cen, PY,
                                        PZ, dc, cnt, h->maxM, h->maxK, st);
         launch_sums<double>(PY, PZ, Es, ws, cnt, dc, dc, dc, nullptr, h->d_cvec, h->d_cvec + dc,
                             h->d_cvec + 2 * dc, nullptr, false, st);
@@ -506,7 +510,7 @@ blm_status project_dev(blm_handle* h, const T* O, const T* G, const T* E, const 
       float* PZ = (float*)h->d_scrZ;
       {
         Prof pr(h, PC_PROJECT, 2);
-        launch_project<float, float>(Os, Gs, ld, ld, h->d_shift, h->d_pbB, h->nb, h->d_cen, PY,
+        launch_project<float, float>(Os, Gs, ld, ld, h->d_shift, h->d_shift32, h->d_pbB, h->nb, h->d_cen, PY,
                                      PZ, dc, cnt, h->maxM, h->maxK, st);
         launch_sums<float>(PY, PZ, Es, ws, cnt, dc, dc, dc, nullptr, h->d_cvec, h->d_cvec + dc,
                            h->d_cvec + 2 * dc, nullptr, true, st);
@@ -705,9 +709,10 @@ blm_status blm_create(const blm_problem* p, void* stream, blm_handle** out) {
     std::vector<DirBlock> dbk(h->nb);
     for (int b = 0; b < h->nb; ++b) {
       const int64_t D = h->db[b] + 1;
-      pbB[b] = ProjBlock{h->off[b], h->Mb[b], h->Kb[b], h->oc[b], 0, h->d_B + h->B_off[b], h->Mb[b]};
+      pbB[b] = ProjBlock{h->off[b], h->Mb[b], h->Kb[b], h->oc[b], 0, h->d_B + h->B_off[b], h->Mb[b],
+                         h->d_B32 + h->B_off[b]};
       pbD[b] = ProjBlock{h->off[b], h->Mb[b], h->n_old, b * h->n_old, 0,
-                         h->d_D ? h->d_D + h->off[b] : nullptr, h->n};
+                         h->d_D ? h->d_D + h->off[b] : nullptr, h->n, nullptr};
       ba[b] = BlockAsm{h->off[b], h->Mb[b], h->db[b], b, 0, h->d_C + h->C_off[b],
                        h->d_S + h->SH_off[b], h->d_H + h->SH_off[b]};
       ep[b] = EigProblem{(int)D, h->Kb[b], 0, 0, h->d_S + h->SH_off[b], h->d_H + h->SH_off[b],
@@ -801,6 +806,7 @@ blm_status blm_block_solve(blm_handle* h) {
   {
     Prof pr(h, PC_DIRS, h->shift != 0.0 ? 3 : 2);
     launch_extract_dirs(h->d_dirb, h->nb, st);
+    if (h->in_type == BLM_IN_F32) launch_to_f32(h->d_B, h->d_B32, h->B_words, st);
     launch_cen(h->d_pbB, h->nb, h->d_vec, h->d_scal, h->d_cen, st);
     if (h->shift != 0.0) {
       BLM_CU(h, cudaMemsetAsync(h->d_cgram, 0, 8 * h->dc * h->dc, st));

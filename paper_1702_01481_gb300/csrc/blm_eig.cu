@@ -544,6 +544,19 @@ __device__ void warp_back_transform(const double* Rt, const double* hbeta, const
 }
 
 
+// Phase timing of dense_geig (debug builds with -DBLM_EIG_TIMING): clock64 marks printed by
+// thread 0 of the first problem of a launch.
+#ifdef BLM_EIG_TIMING
+#define EIG_MARK(i)                                  \
+  do {                                               \
+    if (threadIdx.x == 0) tmark[i] = clock64();      \
+  } while (0)
+#else
+#define EIG_MARK(i) \
+  do {              \
+  } while (0)
+#endif
+
 // Dense solver for one problem, run by the whole CTA (dsm: up to 200 KB of shared memory).
 __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
   const int m = pb.m;
@@ -565,6 +578,10 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
   int* psw = reinterpret_cast<int*>(plw + (int64_t)kVecWarps * 2 * m);   // kVecWarps x m ints
   double* cvec = plw + (int64_t)kVecWarps * 3 * m;            // kMaxKeep x 2m
 
+#ifdef BLM_EIG_TIMING
+  long long tmark[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#endif
+  EIG_MARK(0);
   if (t == 0) {
     sh.iscal[1] = ST_OK;
     sh.iscal[4] = 0;
@@ -594,6 +611,7 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
     if (t == 0) *pb.status = sh.iscal[1];
     return;
   }
+  EIG_MARK(1);
   // ---- 2a. Cholesky (right-looking, lower) ----
   for (int k = 0; k < m; ++k) {
     if (t == 0) {
@@ -660,6 +678,7 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
     }
     __syncthreads();
   }
+  EIG_MARK(2);
   // ---- 3. Householder reduction to Hessenberg form ----
   for (int k = 0; k < m - 2; ++k) {
     double part = 0.0;
@@ -721,6 +740,7 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
   }
   const double anorm = fmax(block_max(amx, sh.red), 1e-300);
   const int want = pb.mode == 1 ? 1 : pb.k;
+  EIG_MARK(3);
   // ---- 4. all eigenvalues, FP64 QR ----
   const bool ok = hqr_windowed(W, m, wr, wi, anorm, dsm, sh);
   __syncthreads();
@@ -794,6 +814,7 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
   }
   const int nsel = sh.iscal[2];
   const int njob = sh.iscal[3];
+  EIG_MARK(4);
   // ---- 5. eigenvectors of the Hessenberg matrix: inverse iteration, one warp per job ----
   // The shift is the QR eigenvalue (accurate to rounding), so three solves from a fixed start
   // vector converge; the residual ||Hh y - lambda y|| is checked before the vector is used.
@@ -888,6 +909,7 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
     if (t == 0) *pb.status = ST_NOCONV;
     return;
   }
+  EIG_MARK(5);
   // ---- 6. back-transformation v = D L^-T Q y, one warp per selected direction ----
   // A complex eigenvector is rotated so that its largest-magnitude component is real and
   // positive; its real part (kept alone when N_K ends inside the pair) is then well defined.
@@ -940,6 +962,13 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
   }
   __syncthreads();
   if (t == 0) *pb.status = (nsel == (pb.mode == 1 ? 1 : pb.k)) ? ST_OK : ST_NOCONV;
+  EIG_MARK(6);
+#ifdef BLM_EIG_TIMING
+  if (t == 0 && blockIdx.x == 0)
+    printf("eig timing m=%d: scale %lld chol+std %lld hess %lld qr %lld vec %lld back %lld cycles\n",
+           m, tmark[1] - tmark[0], tmark[2] - tmark[1], tmark[3] - tmark[2], tmark[4] - tmark[3],
+           tmark[5] - tmark[4], tmark[6] - tmark[5]);
+#endif
 }
 
 __global__ void __launch_bounds__(kEigThreads)

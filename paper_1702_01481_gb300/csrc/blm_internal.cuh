@@ -55,6 +55,7 @@ struct ProjBlock {
   int32_t pad;
   const double* dir; // nd rows of m values, row stride dld
   int64_t dld;
+  const float* dir32;  // the same rows in FP32 (mixed path), or nullptr
 };
 
 enum { ST_OK = 0, ST_NOT_PD = 1, ST_NONFINITE = 2, ST_COMPLEX = 3, ST_NOCONV = 4, ST_ALPHA = 5,
@@ -73,8 +74,11 @@ void launch_contract(const Seg* segs, const Tile* tiles, int ntiles, const SrcAr
                      int64_t ns, int splits, cudaStream_t st);
 template <typename T, typename TO>
 void launch_project(const T* O, const T* G, int64_t ldo, int64_t ldg, const double* shift,
+                    const float* shift32,
                     const ProjBlock* blocks, int nblocks, const double* cen, TO* Y, TO* Z,
                     int64_t ldout, int64_t ns, int max_m, int max_nd, cudaStream_t st);
+// dst[i] = (float)src[i], i < count
+void launch_to_f32(const double* src, float* dst, int64_t count, cudaStream_t st);
 
 // ------------------------------- launchers (blm_sweep_tc.cu) ---------------------------------
 // Split-BF16 tcgen05 accumulation: for each tile, rows [row0, row0 + 128) and columns

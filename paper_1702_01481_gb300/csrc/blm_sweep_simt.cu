@@ -244,6 +244,166 @@ project_kernel(const T* __restrict__ O, const T* __restrict__ G, int64_t ldo, in
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Register-tiled projection (same results as project_kernel, for up to 32 directions).  A CTA
+// takes 128 samples of one block; thread (sg, dg) owns samples 4 sg .. 4 sg + 3 and directions
+// 4 dg .. 4 dg + 3 of both Y = O'.B - cen and Z = G.B (32 accumulators), so each value read from
+// shared memory feeds four FMAs.  Runs of kC parameters are staged by cp.async, two stages in
+// flight; the FP64 directions and shift are converted to the accumulation type as they are
+// staged.  Rows are padded to an odd length so that the lanes of a warp, which read up to eight
+// different sample rows, hit different banks.
+// ---------------------------------------------------------------------------------------------
+constexpr int kTSp = 128;
+template <typename A>
+struct ProjCfg {
+  static constexpr int kC = sizeof(A) == 4 ? 64 : 32;   // parameters per run
+  static constexpr int kL = kC + 1;                     // padded row length
+};
+
+template <typename T, typename A>
+constexpr size_t proj_tiled_smem() {
+  return sizeof(T) * 2 * 2 * kTSp * ProjCfg<A>::kL + sizeof(A) * 2 * (32 * ProjCfg<A>::kL + ProjCfg<A>::kC);
+}
+
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int sz = valid ? (int)sizeof(T) : 0;   // 0: zero-fill
+  if (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(sz) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(sz) : "memory");
+}
+
+template <typename T, typename A, typename TO>
+__global__ void __launch_bounds__(kThreads)
+project_tiled_kernel(const T* __restrict__ O, const T* __restrict__ G, int64_t ldo, int64_t ldg,
+                     const double* __restrict__ shift, const float* __restrict__ shift32,
+                     const ProjBlock* __restrict__ blocks,
+                     const double* __restrict__ cen, TO* __restrict__ Y, TO* __restrict__ Z,
+                     int64_t ldout, int64_t ns) {
+  constexpr int kC = ProjCfg<A>::kC, kL = ProjCfg<A>::kL;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Os = reinterpret_cast<T*>(smem_raw);                    // [2][kTSp][kL]
+  T* Gs = Os + 2 * kTSp * kL;                                 // [2][kTSp][kL]
+  A* Ds = reinterpret_cast<A*>(Gs + 2 * kTSp * kL);           // [2][32][kL]
+  A* Sh = Ds + 2 * 32 * kL;                                   // [2][kC]
+  const ProjBlock pb = blocks[blockIdx.y];
+  const int64_t s_base = (int64_t)blockIdx.x * kTSp;
+  const int t = threadIdx.x;
+  const int dgn = (pb.nd + 3) >> 2;                           // direction groups (<= 8)
+  const bool active = t < 32 * dgn;
+  const int sg = active ? t / dgn : 0, dg = active ? t % dgn : 0;
+  const int nruns = (pb.m + kC - 1) / kC;
+
+  auto issue = [&](int r) {
+    const int st = r & 1;
+    const int p0 = r * kC;
+    const int pc = min(kC, pb.m - p0);
+    T* os = Os + st * kTSp * kL;
+    T* gs = Gs + st * kTSp * kL;
+    for (int idx = t; idx < kTSp * kC; idx += kThreads) {
+      const int k = idx / kC, c = idx - k * kC;
+      const int64_t s = s_base + k;
+      const bool ok = (s < ns) && (c < pc);
+      const int64_t col = pb.lo + p0 + (c < pc ? c : 0);
+      const int64_t srow = s < ns ? s : 0;
+      cp_async_elem(os + k * kL + c, O + srow * ldo + col, ok);
+      cp_async_elem(gs + k * kL + c, G + srow * ldg + col, ok);
+    }
+    // directions and shift in the accumulation type when memory holds them so (cp.async),
+    // else converted on the way
+    const A* dirA = nullptr;
+    const A* shA = nullptr;
+    if constexpr (sizeof(A) == 4) {
+      dirA = reinterpret_cast<const A*>(pb.dir32);
+      shA = reinterpret_cast<const A*>(shift32);
+    } else {
+      dirA = reinterpret_cast<const A*>(pb.dir);
+      shA = reinterpret_cast<const A*>(shift);
+    }
+    A* ds = Ds + st * 32 * kL;
+    for (int idx = t; idx < 32 * kC; idx += kThreads) {
+      const int j = idx / kC, c = idx - j * kC;
+      const bool ok = j < pb.nd && c < pc;
+      const int64_t off = ok ? (int64_t)j * pb.dld + p0 + c : 0;
+      if (dirA)
+        cp_async_elem(ds + j * kL + c, dirA + off, ok);
+      else
+        ds[j * kL + c] = ok ? (A)pb.dir[off] : (A)0;
+    }
+    for (int c = t; c < kC; c += kThreads) {
+      const bool ok = shift != nullptr && c < pc;
+      const int64_t off = ok ? pb.lo + p0 + c : 0;
+      if (shA)
+        cp_async_elem(Sh + st * kC + c, shA + off, ok);
+      else
+        Sh[st * kC + c] = ok ? (A)shift[off] : (A)0;
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+
+  A accY[4][4], accZ[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) accY[i][j] = accZ[i][j] = (A)0;
+
+  issue(0);
+  for (int r = 0; r < nruns; ++r) {
+    if (r + 1 < nruns) {
+      issue(r + 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+    if (active) {
+      const int st = r & 1;
+      const T* os = Os + st * kTSp * kL + (4 * sg) * kL;
+      const T* gs = Gs + st * kTSp * kL + (4 * sg) * kL;
+      const A* ds = Ds + st * 32 * kL + (4 * dg) * kL;
+      const A* sh = Sh + st * kC;
+      const int pc = min(kC, pb.m - r * kC);
+#pragma unroll 2
+      for (int c = 0; c < pc; ++c) {
+        const A shc = sh[c];
+        A o[4], g[4], d[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          o[i] = (A)os[i * kL + c] - shc;
+          g[i] = (A)gs[i * kL + c];
+          d[i] = ds[i * kL + c];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            accY[i][j] = fma(d[j], o[i], accY[i][j]);
+            accZ[i][j] = fma(d[j], g[i], accZ[i][j]);
+          }
+      }
+    }
+    __syncthreads();
+  }
+  if (!active) return;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t s = s_base + 4 * sg + i;
+    if (s >= ns) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int jj = 4 * dg + j;
+      if (jj >= pb.nd) continue;
+      const int64_t oc = pb.oc + jj;
+      A y = accY[i][j];
+      if (cen) y -= (A)cen[oc];
+      Y[s * ldout + oc] = (TO)y;
+      Z[s * ldout + oc] = (TO)accZ[i][j];
+    }
+  }
+}
+
 int splits_for(int64_t ns, int64_t granule, int64_t max_splits) {
   int64_t s = (ns + granule - 1) / granule;
   if (s > max_splits) s = max_splits;
@@ -293,17 +453,39 @@ void launch_contract(const Seg* segs, const Tile* tiles, int ntiles, const SrcAr
 
 template <typename T, typename TO>
 void launch_project(const T* O, const T* G, int64_t ldo, int64_t ldg, const double* shift,
-                    const ProjBlock* blocks, int nblocks, const double* cen, TO* Y, TO* Z,
+                    const float* shift32, const ProjBlock* blocks, int nblocks, const double* cen, TO* Y, TO* Z,
                     int64_t ldout, int64_t ns, int max_m, int max_nd, cudaStream_t st) {
   (void)max_m;
   if (ns <= 0 || nblocks <= 0) return;
   using A = TO;   // FP64 path: FP64 throughout; mixed path: FP32 products and sums
+  if (max_nd <= 32) {
+    constexpr size_t smem_t = proj_tiled_smem<T, A>();
+    cudaFuncSetAttribute(project_tiled_kernel<T, A, TO>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
+    dim3 grid((unsigned)((ns + kTSp - 1) / kTSp), (unsigned)nblocks);
+    project_tiled_kernel<T, A, TO><<<grid, kThreads, smem_t, st>>>(O, G, ldo, ldg, shift, shift32,
+                                                                    blocks, cen, Y, Z, ldout, ns);
+    return;
+  }
   const size_t smem = sizeof(A) * (size_t)(2 * kPS * kPL + max_nd * kPL);
   cudaFuncSetAttribute(project_kernel<T, A, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
   dim3 grid((unsigned)((ns + kPS - 1) / kPS), (unsigned)nblocks);
   project_kernel<T, A, TO><<<grid, kThreads, smem, st>>>(O, G, ldo, ldg, shift, blocks, cen, Y, Z,
                                                          ldout, ns, max_nd);
+}
+
+__global__ void to_f32_kernel(const double* __restrict__ src, float* __restrict__ dst,
+                              int64_t count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
+void launch_to_f32(const double* src, float* dst, int64_t count, cudaStream_t st) {
+  if (count <= 0) return;
+  const int64_t blocks = (count + kThreads - 1) / kThreads;
+  to_f32_kernel<<<(unsigned)(blocks < 1024 ? blocks : 1024), kThreads, 0, st>>>(src, dst, count);
 }
 
 template void launch_colmean<double>(const double*, int64_t, int64_t, int64_t, double*,
@@ -317,15 +499,15 @@ template void launch_sums<float>(const float*, const float*, const float*, const
                                  int64_t, int64_t, int64_t, const double*, double*, double*,
                                  double*, double*, bool, cudaStream_t);
 template void launch_project<double, double>(const double*, const double*, int64_t, int64_t,
-                                             const double*, const ProjBlock*, int, const double*,
+                                             const double*, const float*, const ProjBlock*, int, const double*,
                                              double*, double*, int64_t, int64_t, int, int,
                                              cudaStream_t);
 template void launch_project<float, float>(const float*, const float*, int64_t, int64_t,
-                                           const double*, const ProjBlock*, int, const double*,
+                                           const double*, const float*, const ProjBlock*, int, const double*,
                                            float*, float*, int64_t, int64_t, int, int,
                                            cudaStream_t);
 template void launch_project<float, double>(const float*, const float*, int64_t, int64_t,
-                                            const double*, const ProjBlock*, int, const double*,
+                                            const double*, const float*, const ProjBlock*, int, const double*,
                                             double*, double*, int64_t, int64_t, int, int,
                                             cudaStream_t);
 
