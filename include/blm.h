@@ -148,6 +148,30 @@ blm_status blm_profile(blm_handle* h, int enable);
 blm_status blm_profile_read(blm_handle* h, int n, double* ms, int64_t* launches);
 const char* blm_profile_class_name(int i);
 
+/* Allocation-free solve of one block problem.  The paper has no counterpart: this is an
+ * interface for callers that cannot allocate device memory when they need a block solved (a
+ * VMC program that reserves the whole device at start-up and then forbids cudaMalloc, code that
+ * must avoid the device-wide synchronisation cudaMalloc/cudaFree may imply, or a runtime that
+ * only lends the library pointers it already owns).
+ *
+ * Same computation as blm_block_solve for a block without history directions: solves
+ * H v = lambda S v (S, H: device, row-major dim x dim, the block's overlap and Hamiltonian
+ * including row/column 0) and writes the n_keep lowest eigenvalues (real parts) into lambda
+ * (device, n_keep) and the corresponding directions into B (device, n_keep x (dim - 1),
+ * unit 2-norm, largest-magnitude entry positive), exactly as blm_get_block reports them.
+ *
+ * Workspace: a static device array inside the library (about 7.2 MB, held by every GPU that
+ * loads the library until the process exits); nothing is allocated or freed.  Limits: 2 <= dim
+ * <= blm_noalloc_max_dim() (257), 1 <= n_keep <= min(64, dim - 1); larger sizes return
+ * BLM_ERR_ARG with a message on stderr.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Every call shares the one array: calls that overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller.  Runs on `stream` and
+ * synchronises it; BLM_ERR_NUMERIC if the overlap is not positive definite or the solve fails. */
+int32_t blm_noalloc_max_dim(void);
+blm_status blm_block_solve_noalloc(const double* S, const double* H, int32_t dim, int32_t n_keep,
+                                   double* lambda, double* B, void* stream);
+
 /* Device bytes blm_create allocates for this problem (0 if the problem is invalid).  Host
  * function: needs no GPU. */
 size_t blm_memory_estimate(const blm_problem* problem);

@@ -59,6 +59,9 @@ _sig = {
     "blm_profile": (ctypes.c_int, [_H, ctypes.c_int]),
     "blm_profile_read": (ctypes.c_int, [_H, ctypes.c_int, _P, _P]),
     "blm_profile_class_name": (ctypes.c_char_p, [ctypes.c_int]),
+    "blm_noalloc_max_dim": (ctypes.c_int32, []),
+    "blm_block_solve_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P,
+                                               ctypes.c_void_p]),
 }
 BLM_PROF_CLASSES = 12
 for _name, (_res, _args) in _sig.items():
@@ -178,6 +181,18 @@ def blm_profile_read(h):
     n = (ctypes.c_int64 * BLM_PROF_CLASSES)()
     _check(h, _lib.blm_profile_read(h, BLM_PROF_CLASSES, ms, n), "blm_profile_read")
     return {_lib.blm_profile_class_name(i).decode(): (ms[i], n[i]) for i in range(BLM_PROF_CLASSES)}
+
+
+def blm_noalloc_max_dim():
+    return int(_lib.blm_noalloc_max_dim())
+
+
+def blm_block_solve_noalloc(S, H, dim, n_keep, lam, B, stream=0):
+    """One block problem through the allocation-free entry point (device arrays)."""
+    st = _lib.blm_block_solve_noalloc(_ptr(S), _ptr(H), int(dim), int(n_keep), _ptr(lam), _ptr(B),
+                                      ctypes.c_void_p(int(stream)))
+    if st != BLM_OK:
+        raise BLMError(st, "blm_block_solve_noalloc")
 
 
 # ----- convenience wrapper ---------------------------------------------------------------------

@@ -1173,3 +1173,129 @@ void launch_eig(const EigProblem* probs, int nprob, int threads, cudaStream_t st
 }
 
 }  // namespace blm
+
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free block solve.
+//
+// Some callers cannot allocate device memory when they need a block solved: a VMC program that
+// reserves the whole device for its walkers at start-up and then forbids further cudaMalloc,
+// code that must not take the device-wide synchronisation that cudaMalloc/cudaFree can imply,
+// or a host runtime that only hands this library pointers it already owns.  For them,
+// blm_block_solve_noalloc runs the same dense solver as blm_block_solve on one block problem
+// whose overlap and Hamiltonian the caller supplies, with its workspace in the file-scope array
+// below (held by every GPU that loads the library until the process exits).
+// ---------------------------------------------------------------------------------------------
+namespace blm {
+namespace {
+
+constexpr int kNoAllocMaxDim = 257;     // block problems up to 1 + 256 parameters
+constexpr int kNoAllocMaxKeep = 64;
+constexpr size_t kNoAllocWork = (size_t)eig_total_doubles(kNoAllocMaxDim);
+// workspace | eigenvectors (kNoAllocMaxKeep x kNoAllocMaxDim) | status word
+constexpr size_t kNoAllocDoubles = kNoAllocWork + (size_t)kNoAllocMaxKeep * kNoAllocMaxDim + 8;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+__global__ void __launch_bounds__(kEigThreads)
+noalloc_block_kernel(double* scratch, const double* S, const double* H, int dim, int keep,
+                     double* lambda, double* B) {
+  extern __shared__ double dsm[];
+  __shared__ Shared sh;
+  __shared__ double red[32];
+  double* work = scratch;
+  double* vec = scratch + kNoAllocWork;
+  int32_t* status = reinterpret_cast<int32_t*>(vec + (size_t)kNoAllocMaxKeep * kNoAllocMaxDim);
+  if (threadIdx.x == 0) *status = ST_OK;     // the array keeps the previous call's contents
+  __syncthreads();
+  EigProblem pb{dim, keep, 0, 0, S, H, work, lambda, vec, status};
+  dense_geig(pb, dsm, sh);
+  __syncthreads();
+  if (*status != ST_OK) return;
+  // rows of B: beta parts of the eigenvectors, unit 2-norm, largest-magnitude entry positive
+  const int m = dim - 1;
+  for (int q = 0; q < keep; ++q) {
+    const double* v = vec + (size_t)q * dim + 1;
+    double part = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) part += v[i] * v[i];
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double n2 = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) n2 += red[w];
+      int best = 0;
+      for (int i = 1; i < m; ++i)
+        if (fabs(v[i]) > fabs(v[best])) best = i;
+      red[0] = (n2 > 0.0) ? (v[best] < 0.0 ? -1.0 : 1.0) / sqrt(n2) : 0.0;
+      if (!(n2 > 0.0)) *status = ST_ZERO_DIR;
+    }
+    __syncthreads();
+    const double sc = red[0];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) B[(size_t)q * m + i] = v[i] * sc;
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+}  // namespace blm
+
+#include <mutex>
+
+namespace {
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[256] = {nullptr};
+}  // namespace
+
+extern "C" {
+
+int32_t blm_noalloc_max_dim(void) { return blm::kNoAllocMaxDim; }
+
+blm_status blm_block_solve_noalloc(const double* S, const double* H, int32_t dim,
+                                   int32_t n_keep, double* lambda, double* B, void* stream) {
+  if (!S || !H || !lambda || !B) return BLM_ERR_ARG;
+  if (dim < 2 || dim > blm::kNoAllocMaxDim) {
+    fprintf(stderr, "blm_block_solve_noalloc: dimension %d outside 2..%d (the static workspace "
+                    "holds block problems up to %d)\n", dim, blm::kNoAllocMaxDim, blm::kNoAllocMaxDim);
+    return BLM_ERR_ARG;
+  }
+  if (n_keep < 1 || n_keep > dim - 1 || n_keep > blm::kNoAllocMaxKeep) {
+    fprintf(stderr, "blm_block_solve_noalloc: n_keep %d outside 1..%d\n", n_keep,
+            dim - 1 < blm::kNoAllocMaxKeep ? dim - 1 : blm::kNoAllocMaxKeep);
+    return BLM_ERR_ARG;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return BLM_ERR_CUDA;
+  double* scratch = nullptr;
+  {
+    // once per device, with that device current: the array's device address
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, blm::g_noalloc_scratch) != cudaSuccess) {
+        cudaGetLastError();
+        return BLM_ERR_CUDA;
+      }
+      g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int smem = 200 * 1024;
+  if (cudaFuncSetAttribute(blm::noalloc_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem) != cudaSuccess)
+    return BLM_ERR_CUDA;
+  blm::noalloc_block_kernel<<<1, blm::kEigThreads, smem, st>>>(scratch, S, H, dim, n_keep,
+                                                               lambda, B);
+  if (cudaGetLastError() != cudaSuccess) return BLM_ERR_CUDA;
+  int32_t status = 0;
+  const int32_t* dstat = reinterpret_cast<const int32_t*>(
+      scratch + blm::kNoAllocWork + (size_t)blm::kNoAllocMaxKeep * blm::kNoAllocMaxDim);
+  if (cudaMemcpyAsync(&status, dstat, sizeof(status), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return BLM_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return BLM_ERR_CUDA;
+  return status == blm::ST_OK ? BLM_OK : BLM_ERR_NUMERIC;
+}
+
+}  // extern "C"
