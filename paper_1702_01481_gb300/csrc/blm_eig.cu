@@ -97,6 +97,88 @@ __device__ __forceinline__ double rsqrt_nr(double a) {
   return r;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Double-word arithmetic: a value is the unevaluated sum hi + lo of two FP32 numbers with
+// |lo| <= ulp(hi) / 2, about 48 significant bits.  On this GPU an FP32 operation has ~4.6 cycles
+// of latency against FP64's 65, and the SM's FP32 throughput is ~64x its FP64 throughput, so the
+// latency-bound QR sweep runs on double words.  The operations are the error-free transforms
+// TwoSum (Knuth), Fast2Sum (Dekker) and the FMA-based exact product, combined as in the
+// double-word addition and multiplication algorithms of Joldes, Muller and Popescu (ACM TOMS 44,
+// 2017): relative error of an addition <= 3u^2, of a multiplication <= 5u^2, u = 2^-24.
+// Explicit _rn intrinsics keep the compiler from contracting or reassociating them.
+// ---------------------------------------------------------------------------------------------
+struct dw {
+  float hi, lo;
+};
+__device__ __forceinline__ dw dw_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return dw{s, e};
+}
+__device__ __forceinline__ dw dw_fast_two_sum(float a, float b) {   // |a| >= |b| or a = 0
+  const float s = __fadd_rn(a, b);
+  return dw{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dw operator+(dw x, dw y) {
+  const dw s = dw_two_sum(x.hi, y.hi);
+  const dw t = dw_two_sum(x.lo, y.lo);
+  dw u = dw_fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return dw_fast_two_sum(u.hi, __fadd_rn(u.lo, t.lo));
+}
+__device__ __forceinline__ dw operator-(dw x) { return dw{-x.hi, -x.lo}; }
+__device__ __forceinline__ dw operator-(dw x, dw y) { return x + (-y); }
+__device__ __forceinline__ dw operator*(dw x, dw y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, e));
+  return dw_fast_two_sum(p, e);
+}
+__device__ __forceinline__ dw dw_of(float a) { return dw{a, 0.0f}; }
+__device__ __forceinline__ dw dw_of_double(double d) {
+  const float h = __double2float_rn(d);
+  return dw{h, __double2float_rn(d - (double)h)};
+}
+__device__ __forceinline__ double to_double(dw x) { return (double)x.hi + (double)x.lo; }
+__device__ __forceinline__ double to_double(double x) { return x; }
+__device__ __forceinline__ float mag(dw x) { return fabsf(x.hi); }
+__device__ __forceinline__ double mag(double x) { return fabs(x); }
+__device__ __forceinline__ dw dw_abs(dw x) { return x.hi < 0.0f ? -x : x; }
+__device__ __forceinline__ dw dw_scale(dw x, float p2) { return dw{x.hi * p2, x.lo * p2}; }  // p2 = 2^k
+
+// Householder reflector of house3 in double words.  (x, y, z) is first scaled by a power of two
+// near 1 / max(|x|, |y|, |z|) so that no square under- or overflows FP32; 1/sqrt and 1/x use an
+// FP32 seed and two Newton-Raphson steps carried out in double words.
+__device__ void house3(dw x, dw y, dw z, dw& beta, dw& v1, dw& v2, dw& alpha) {
+  const float amax = fmaxf(mag(x), fmaxf(mag(y), mag(z)));
+  if (mag(y) == 0.0f && mag(z) == 0.0f) {
+    beta = v1 = v2 = dw_of(0.0f);
+    alpha = x;
+    return;
+  }
+  int ex;
+  frexpf(amax, &ex);
+  const float f = ldexpf(1.0f, -ex), finv = ldexpf(1.0f, ex);
+  x = dw_scale(x, f);
+  y = dw_scale(y, f);
+  z = dw_scale(z, f);
+  const dw n2 = x * x + (y * y + z * z);                 // in [1/4, 3]
+  dw rho = dw_of(rsqrtf(n2.hi));
+  for (int it = 0; it < 2; ++it) {
+    const dw e = dw_of(1.0f) - n2 * (rho * rho);
+    rho = rho + dw_scale(rho * e, 0.5f);
+  }
+  const dw mu = n2 * rho;
+  const bool neg = x.hi < 0.0f;
+  const dw v0 = neg ? x - mu : x + mu;
+  dw r = dw_of(__frcp_rn(v0.hi));
+  for (int it = 0; it < 2; ++it) r = r + r * (dw_of(1.0f) - v0 * r);
+  v1 = y * r;
+  v2 = z * r;
+  beta = dw_of(1.0f) + dw_abs(x) * rho;
+  alpha = dw_scale(neg ? mu : -mu, finv);
+}
+
 // 3-vector (or 2-vector) Householder reflector P = I - beta v v^T, v = (1, v1, v2), with
 // P (x, y, z)^T = (alpha, 0, 0)^T, alpha = -sign(x) ||(x, y, z)||.  With mu = ||(x, y, z)|| and
 // v0 = x + sign(x) mu (no cancellation), v = (v0, y, z) / v0 and beta = 2 v0^2 / (v0^2 + y^2 + z^2)
@@ -162,23 +244,41 @@ __device__ __forceinline__ void chase_sync() {
 // shared memory the QR needs: the window and the reflectors of one window
 constexpr int kQrSmemDoubles = kWin * kWinLd + 3 * kWin;
 
-__device__ bool hqr_windowed(double* G, int m, double* wr, double* wi, double anorm, double* dsm,
+// Arithmetic of the QR sweep: FP64, or double words (default; FP64 when it fails).
+template <typename R>
+struct QrArith;
+template <>
+struct QrArith<double> {
+  static constexpr double kEps = 2.220446049250313e-16;   // deflation threshold (relative)
+  __device__ static double of(double d) { return d; }
+};
+template <>
+struct QrArith<dw> {
+  static constexpr double kEps = 3.0e-14;                 // above the double-word rounding noise
+  __device__ static dw of(double d) { return dw_of_double(d); }
+};
+
+template <typename R>
+__device__ bool hqr_windowed(R* G, int m, double* wr, double* wi, double anorm, double* dsm,
                              Shared& sh) {
+  using Q = QrArith<R>;
   const int t = threadIdx.x, nt = blockDim.x;
-  const double eps = 2.220446049250313e-16;
-  double* win = dsm;
-  double* refl = dsm + kWin * kWinLd;
+  const double eps = Q::kEps;
+  R* win = reinterpret_cast<R*>(dsm);
+  R* refl = win + kWin * kWinLd;
+  const R zero = Q::of(0.0);
   int hi = m - 1;
   int its = 0, total = 0;
   const int limit = 40 * m + 100;
+  auto g = [&](int i, int j) -> R& { return G[(int64_t)i * m + j]; };
   while (hi >= 0) {
     // --- deflation: the largest i in [1, hi] whose subdiagonal entry is negligible ---
     if (t == 0) sh.iscal[0] = 0;
     __syncthreads();
     for (int i = hi - t; i >= 1; i -= nt) {
-      double s = fabs(G[(int64_t)(i - 1) * m + i - 1]) + fabs(G[(int64_t)i * m + i]);
+      double s = (double)mag(g(i - 1, i - 1)) + (double)mag(g(i, i));
       if (s == 0.0) s = anorm;
-      if (fabs(G[(int64_t)i * m + i - 1]) <= eps * s) {
+      if ((double)mag(g(i, i - 1)) <= eps * s) {
         atomicMax(&sh.iscal[0], i);
         break;
       }
@@ -187,13 +287,13 @@ __device__ bool hqr_windowed(double* G, int m, double* wr, double* wi, double an
     const int l = sh.iscal[0];
     if (l == hi || l == hi - 1) {
       if (t == 0) {
-        if (l > 0) G[(int64_t)l * m + l - 1] = 0.0;
+        if (l > 0) g(l, l - 1) = zero;
         if (l == hi) {
-          wr[hi] = G[(int64_t)hi * m + hi];
+          wr[hi] = to_double(g(hi, hi));
           wi[hi] = 0.0;
         } else {
-          const double a = G[(int64_t)(hi - 1) * m + hi - 1], b = G[(int64_t)(hi - 1) * m + hi];
-          const double c = G[(int64_t)hi * m + hi - 1], d = G[(int64_t)hi * m + hi];
+          const double a = to_double(g(hi - 1, hi - 1)), b = to_double(g(hi - 1, hi));
+          const double c = to_double(g(hi, hi - 1)), d = to_double(g(hi, hi));
           const double p = 0.5 * (a - d);
           const double disc = p * p + b * c;
           const double mid = 0.5 * (a + d);
@@ -224,22 +324,24 @@ __device__ bool hqr_windowed(double* G, int m, double* wr, double* wi, double an
     ++total;
     // --- shifts and the first column of the double-shift polynomial (thread 0) ---
     if (t == 0) {
-      if (l > 0) G[(int64_t)l * m + l - 1] = 0.0;
-      auto g = [&](int i, int j) { return G[(int64_t)i * m + j]; };
-      double s, tt;
+      if (l > 0) g(l, l - 1) = zero;
+      R s, tt;
       if (its % 11 == 10) {
-        const double e = fabs(g(hi, hi - 1)) + fabs(g(hi - 1, hi - 2));
-        s = 1.5 * e;
+        const R e = Q::of((double)mag(g(hi, hi - 1)) + (double)mag(g(hi - 1, hi - 2)));
+        s = Q::of(1.5) * e;
         tt = e * e;
       } else {
         s = g(hi - 1, hi - 1) + g(hi, hi);
         tt = g(hi - 1, hi - 1) * g(hi, hi) - g(hi - 1, hi) * g(hi, hi - 1);
       }
-      const double h00 = g(l, l), h10 = g(l + 1, l), h01 = g(l, l + 1);
-      const double h11 = g(l + 1, l + 1), h21 = g(l + 2, l + 1);
-      sh.scal[0] = h00 * h00 + h01 * h10 - s * h00 + tt;
-      sh.scal[1] = h10 * (h00 + h11 - s);
-      sh.scal[2] = h10 * h21;
+      const R h00 = g(l, l), h10 = g(l + 1, l), h01 = g(l, l + 1);
+      const R h11 = g(l + 1, l + 1), h21 = g(l + 2, l + 1);
+      const R x0 = h00 * h00 + h01 * h10 - s * h00 + tt;
+      const R y0 = h10 * (h00 + h11 - s);
+      const R z0 = h10 * h21;
+      sh.scal[0] = to_double(x0);
+      sh.scal[1] = to_double(y0);
+      sh.scal[2] = to_double(z0);
     }
     __syncthreads();
     // --- the sweep, window by window ---
@@ -250,72 +352,73 @@ __device__ bool hqr_windowed(double* G, int m, double* wr, double* wi, double an
       const int w = b - a + 1;
       for (int idx = t; idx < w * w; idx += nt) {
         const int r = idx / w, c = idx - r * w;
-        win[r * kWinLd + c] = G[(int64_t)(a + r) * m + a + c];
+        win[r * kWinLd + c] = g(a + r, a + c);
       }
       __syncthreads();
       if (t < kChase) {
-        auto W = [&](int i, int j) -> double& { return win[(i - a) * kWinLd + (j - a)]; };
+        auto W = [&](int i, int j) -> R& { return win[(i - a) * kWinLd + (j - a)]; };
         for (int k = ks; k <= ke; ++k) {
           const bool three = (k <= hi - 2);
-          double x, y, z;
+          R x, y, z;
           if (k == l) {
-            x = sh.scal[0];
-            y = sh.scal[1];
-            z = sh.scal[2];
+            x = Q::of(sh.scal[0]);
+            y = Q::of(sh.scal[1]);
+            z = Q::of(sh.scal[2]);
           } else {
             x = W(k, k - 1);
             y = W(k + 1, k - 1);
-            z = three ? W(k + 2, k - 1) : 0.0;
+            z = three ? W(k + 2, k - 1) : zero;
           }
-          double beta, v1, v2, alpha;
-          house3(x, y, three ? z : 0.0, beta, v1, v2, alpha);
-          if (!three) v2 = 0.0;
-          const double bv1 = beta * v1, bv2 = beta * v2;
+          R beta, v1, v2, alpha;
+          house3(x, y, three ? z : zero, beta, v1, v2, alpha);
+          if (!three) v2 = zero;
+          const R bv1 = beta * v1, bv2 = beta * v2;
+          const bool act = mag(beta) != 0;
           if (t == 0) {
             refl[3 * (k - ks)] = beta;
             refl[3 * (k - ks) + 1] = v1;
             refl[3 * (k - ks) + 2] = v2;
           }
-          if (beta != 0.0) {
+          if (act) {
             // rows k..k+2, columns k..b (the bulge column k-1 is set below)
             for (int j = k + t; j <= b; j += kChase) {
-              double& r0 = W(k, j);
-              double& r1 = W(k + 1, j);
+              R& r0 = W(k, j);
+              R& r1 = W(k + 1, j);
               if (three) {
-                double& r2 = W(k + 2, j);
-                const double p = r0 + fma(v1, r1, v2 * r2);
-                r0 = fma(-beta, p, r0);
-                r1 = fma(-bv1, p, r1);
-                r2 = fma(-bv2, p, r2);
+                R& r2 = W(k + 2, j);
+                const R p = r0 + (v1 * r1 + v2 * r2);
+                r0 = r0 - beta * p;
+                r1 = r1 - bv1 * p;
+                r2 = r2 - bv2 * p;
               } else {
-                const double p = fma(v1, r1, r0);
-                r0 = fma(-beta, p, r0);
-                r1 = fma(-bv1, p, r1);
+                const R p = r0 + v1 * r1;
+                r0 = r0 - beta * p;
+                r1 = r1 - bv1 * p;
               }
             }
           }
           chase_sync();   // every thread has read the bulge column and finished its rows
-          if (beta != 0.0) {
+          if (act) {
             if (t == 0 && k > l) {
               W(k, k - 1) = alpha;
-              W(k + 1, k - 1) = 0.0;
-              if (three) W(k + 2, k - 1) = 0.0;
+              W(k + 1, k - 1) = zero;
+              if (three) W(k + 2, k - 1) = zero;
             }
             // columns k..k+2, rows a..min(k+3, hi)
             const int rmax = three ? min(k + 3, hi) : hi;
             for (int i = a + t; i <= rmax; i += kChase) {
-              double& c0 = W(i, k);
-              double& c1 = W(i, k + 1);
+              R& c0 = W(i, k);
+              R& c1 = W(i, k + 1);
               if (three) {
-                double& c2 = W(i, k + 2);
-                const double p = c0 + fma(v1, c1, v2 * c2);
-                c0 = fma(-beta, p, c0);
-                c1 = fma(-bv1, p, c1);
-                c2 = fma(-bv2, p, c2);
+                R& c2 = W(i, k + 2);
+                const R p = c0 + (v1 * c1 + v2 * c2);
+                c0 = c0 - beta * p;
+                c1 = c1 - bv1 * p;
+                c2 = c2 - bv2 * p;
               } else {
-                const double p = fma(v1, c1, c0);
-                c0 = fma(-beta, p, c0);
-                c1 = fma(-bv1, p, c1);
+                const R p = c0 + v1 * c1;
+                c0 = c0 - beta * p;
+                c1 = c1 - bv1 * p;
               }
             }
           }
@@ -325,29 +428,29 @@ __device__ bool hqr_windowed(double* G, int m, double* wr, double* wi, double an
       __syncthreads();
       for (int idx = t; idx < w * w; idx += nt) {
         const int r = idx / w, c = idx - r * w;
-        G[(int64_t)(a + r) * m + a + c] = win[r * kWinLd + c];
+        g(a + r, a + c) = win[r * kWinLd + c];
       }
       // operations outside the window: columns ks..ke+2 of rows l..a-1 (column operations) and
       // rows ks..ke+2 of columns b+1..hi (row operations)
       const int nfa = a - l, nfb = hi - b;
       for (int u = t; u < nfa + nfb; u += nt) {
         // a row above the window walks right along its columns; a column right of the window
-        // walks down its rows: element (s, e) of the walk is G[base + s * step_s + e]
+        // walks down its rows: element e of the walk is G[base + e * step]
         const bool row_walk = u < nfa;
         const int64_t base = row_walk ? (int64_t)(l + u) * m : (int64_t)(b + 1 + u - nfa);
         const int64_t step = row_walk ? 1 : m;
         // e0..e2: positions k..k+2; q0..q3: positions k+3..k+6 loaded ahead (L2 latency)
-        auto ld = [&](int e) { return (e <= hi) ? G[base + (int64_t)e * step] : 0.0; };
-        double e0 = ld(ks), e1 = ld(ks + 1), e2 = ld(ks + 2);
-        double q0 = ld(ks + 3), q1 = ld(ks + 4), q2 = ld(ks + 5), q3 = ld(ks + 6);
+        auto ld = [&](int e) { return (e <= hi) ? G[base + (int64_t)e * step] : zero; };
+        R e0 = ld(ks), e1 = ld(ks + 1), e2 = ld(ks + 2);
+        R q0 = ld(ks + 3), q1 = ld(ks + 4), q2 = ld(ks + 5), q3 = ld(ks + 6);
         for (int k = ks; k <= ke; ++k) {
-          const double beta = refl[3 * (k - ks)];
-          if (beta != 0.0) {
-            const double v1 = refl[3 * (k - ks) + 1], v2 = refl[3 * (k - ks) + 2];
-            const double p = e0 + fma(v1, e1, v2 * e2);   // v2 = 0 on the last (two-row) step
-            e0 = fma(-beta, p, e0);
-            e1 = fma(-beta * v1, p, e1);
-            e2 = fma(-beta * v2, p, e2);
+          const R beta = refl[3 * (k - ks)];
+          if (mag(beta) != 0) {
+            const R v1 = refl[3 * (k - ks) + 1], v2 = refl[3 * (k - ks) + 2];
+            const R p = e0 + (v1 * e1 + v2 * e2);   // v2 = 0 on the last (two-row) step
+            e0 = e0 - beta * p;
+            e1 = e1 - (beta * v1) * p;
+            e2 = e2 - (beta * v2) * p;
           }
           G[base + (int64_t)k * step] = e0;
           e0 = e1;
@@ -729,25 +832,49 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
     for (int i = k + 2 + t; i < m; i += nt) A[(int64_t)i * m + k] = col[i];
     __syncthreads();
   }
-  // ---- Hessenberg copies: Hh (inverse iteration) and G (QR working copy, in W) ----
+  // ---- Hessenberg copies: Hh (inverse iteration) and the QR working copy in W ----
   double amx = 0.0;
   for (int64_t idx = t; idx < mm; idx += nt) {
     const int i = (int)(idx / m), j = (int)(idx % m);
     const double v = (j >= i - 1) ? A[idx] : 0.0;
     Hh[idx] = v;
-    W[idx] = v;
     amx = fmax(amx, fabs(v));
   }
   const double anorm = fmax(block_max(amx, sh.red), 1e-300);
+  // the QR runs on the matrix scaled by a power of two to max |entry| in [1/2, 1)
+  int gex;
+  frexp(anorm, &gex);
+  const double gscale = ldexp(1.0, -gex);
   const int want = pb.mode == 1 ? 1 : pb.k;
   EIG_MARK(3);
-  // ---- 4. all eigenvalues, FP64 QR ----
-  const bool ok = hqr_windowed(W, m, wr, wi, anorm, dsm, sh);
+  // ---- 4. all eigenvalues: QR in double words; FP64 if that fails ----
+  dw* Wd = reinterpret_cast<dw*>(W);
+  for (int64_t idx = t; idx < mm; idx += nt) Wd[idx] = dw_of_double(Hh[idx] * gscale);
+  if (t == 0) sh.iscal[5] = 1;
   __syncthreads();
+  bool ok = hqr_windowed<dw>(Wd, m, wr, wi, anorm * gscale, dsm, sh);
+  __syncthreads();
+  for (int i = t; i < m; i += nt)
+    if (!isfinite(wr[i]) || !isfinite(wi[i])) sh.iscal[5] = 0;
+  __syncthreads();
+  if (!ok || sh.iscal[5] == 0) {
+#ifdef BLM_EIG_DEBUG
+    if (t == 0) printf("eig: problem %d double-word QR failed, FP64 QR\n", (int)blockIdx.x);
+#endif
+    for (int64_t idx = t; idx < mm; idx += nt) W[idx] = Hh[idx] * gscale;
+    __syncthreads();
+    ok = hqr_windowed<double>(W, m, wr, wi, anorm * gscale, dsm, sh);
+    __syncthreads();
+  }
   if (!ok) {
     if (t == 0) *pb.status = ST_NOCONV;
     return;
   }
+  for (int i = t; i < m; i += nt) {
+    wr[i] /= gscale;
+    wi[i] /= gscale;
+  }
+  __syncthreads();
   // ---- selection of the lowest real parts; eigenvector jobs ----
   // A job is one complex pair (both of its parts) or a run of selected real eigenvalues closer
   // to each other than 1e-9 anorm (a numerically repeated eigenvalue): one warp computes the
@@ -860,14 +987,14 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
             }
           }
         }
-        // normalise, then the residual in cur (re | im)
+        // normalise; H y into cur (re | im); the Rayleigh quotient y^H H y / y^H y becomes the
+        // eigenvalue (FP64 accurate whatever the QR's precision); then the residual
         double nrm = 0.0;
         for (int i = lane; i < m; i += 32) nrm += yv[i] * yv[i] + (cx ? yv[m + i] * yv[m + i] : 0.0);
         nrm = sqrt(warp_sum(nrm));
         const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
         for (int i = lane; i < 2 * m; i += 32) yv[i] = (i < m || cx) ? yv[i] * inv : 0.0;
         __syncwarp();
-        double rr = 0.0;
         for (int i = 0; i < m; ++i) {
           const double* hrow = Hh + (int64_t)i * m;
           double hr = 0.0, hm = 0.0;
@@ -877,16 +1004,35 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
           }
           hr = warp_sum(hr);
           if (cx) hm = warp_sum(hm);
-          const double er = hr - (lre * yv[i] - lim * yv[m + i]);
-          const double ei = cx ? hm - (lre * yv[m + i] + lim * yv[i]) : 0.0;
+          if (lane == 0) {
+            cur[i] = hr;
+            cur[m + i] = hm;
+          }
+        }
+        __syncwarp();
+        double qre = 0.0, qim = 0.0;
+        for (int i = lane; i < m; i += 32) {
+          qre += yv[i] * cur[i] + (cx ? yv[m + i] * cur[m + i] : 0.0);
+          if (cx) qim += yv[i] * cur[m + i] - yv[m + i] * cur[i];
+        }
+        qre = warp_sum(qre);   // y is unit: y^H y = 1
+        qim = cx ? warp_sum(qim) : 0.0;
+        double rr = 0.0;
+        for (int i = lane; i < m; i += 32) {
+          const double er = cur[i] - (qre * yv[i] - qim * yv[m + i]);
+          const double ei = cx ? cur[m + i] - (qre * yv[m + i] + qim * yv[i]) : 0.0;
           rr += er * er + ei * ei;
         }
-        if (lane == 0 && !(sqrt(rr) <= 1e-9 * anorm)) {
-          sh.iscal[4] = 1;
+        rr = warp_sum(rr);
+        if (lane == 0) {
+          if (!(sqrt(rr) <= 1e-9 * anorm) || !(fabs(qre - lre) <= 1e-6 * anorm)) {
+            sh.iscal[4] = 1;
 #ifdef BLM_EIG_DEBUG
-          printf("eig: problem %d eigenvector %d residual %.3e (anorm %.3e)\n", (int)blockIdx.x,
-                 q0 + c, sqrt(rr), anorm);
+            printf("eig: problem %d eigenvector %d residual %.3e shift %.15g quotient %.15g (anorm %.3e)\n",
+                   (int)blockIdx.x, q0 + c, sqrt(rr), lre, qre, anorm);
 #endif
+          }
+          wr[idx] = qre;
         }
         double* dst = cvec + (int64_t)(q0 + c) * 2 * m;
         for (int i = lane; i < 2 * m; i += 32) dst[i] = yv[i];

@@ -246,17 +246,17 @@ project_kernel(const T* __restrict__ O, const T* __restrict__ G, int64_t ldo, in
 
 // ---------------------------------------------------------------------------------------------
 // Register-tiled projection (same results as project_kernel, for up to 32 directions).  A CTA
-// takes 128 samples of one block; thread (sg, dg) owns samples 4 sg .. 4 sg + 3 and directions
-// 4 dg .. 4 dg + 3 of both Y = O'.B - cen and Z = G.B (32 accumulators), so each value read from
-// shared memory feeds four FMAs.  Runs of kC parameters are staged by cp.async, two stages in
-// flight; the FP64 directions and shift are converted to the accumulation type as they are
-// staged.  Rows are padded to an odd length so that the lanes of a warp, which read up to eight
-// different sample rows, hit different banks.
+// takes 128 samples of one block; thread (sg, dg) owns samples 2 sg, 2 sg + 1 and directions
+// DT dg .. DT dg + DT - 1 (DT = 5 for up to 20 directions, 8 for up to 32) of both
+// Y = O'.B - cen and Z = G.B, so all 256 threads compute and each value read from shared memory
+// feeds DT or two FMAs.  Runs of kC parameters are staged by cp.async, two stages in flight,
+// small enough for two CTAs per SM; rows are padded to an odd length so that the eight sample
+// rows a warp reads fall in different banks.
 // ---------------------------------------------------------------------------------------------
 constexpr int kTSp = 128;
 template <typename A>
 struct ProjCfg {
-  static constexpr int kC = sizeof(A) == 4 ? 64 : 32;   // parameters per run
+  static constexpr int kC = sizeof(A) == 4 ? 32 : 16;   // parameters per run
   static constexpr int kL = kC + 1;                     // padded row length
 };
 
@@ -275,8 +275,8 @@ __device__ __forceinline__ void cp_async_elem(T* dst, const T* src, bool valid) 
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(sz) : "memory");
 }
 
-template <typename T, typename A, typename TO>
-__global__ void __launch_bounds__(kThreads)
+template <typename T, typename A, typename TO, int DT>
+__global__ void __launch_bounds__(kThreads, 2)
 project_tiled_kernel(const T* __restrict__ O, const T* __restrict__ G, int64_t ldo, int64_t ldg,
                      const double* __restrict__ shift, const float* __restrict__ shift32,
                      const ProjBlock* __restrict__ blocks,
@@ -291,8 +291,8 @@ project_tiled_kernel(const T* __restrict__ O, const T* __restrict__ G, int64_t l
   const ProjBlock pb = blocks[blockIdx.y];
   const int64_t s_base = (int64_t)blockIdx.x * kTSp;
   const int t = threadIdx.x;
-  const int dgn = (pb.nd + 3) >> 2;                           // direction groups (<= 8)
-  const bool active = t < 32 * dgn;
+  const int dgn = (pb.nd + DT - 1) / DT;                      // direction groups (<= 4)
+  const bool active = t < (kTSp / 2) * dgn;
   const int sg = active ? t / dgn : 0, dg = active ? t % dgn : 0;
   const int nruns = (pb.m + kC - 1) / kC;
 
@@ -343,11 +343,11 @@ project_tiled_kernel(const T* __restrict__ O, const T* __restrict__ G, int64_t l
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
 
-  A accY[4][4], accZ[4][4];
+  A accY[2][DT], accZ[2][DT];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) accY[i][j] = accZ[i][j] = (A)0;
+    for (int j = 0; j < DT; ++j) accY[i][j] = accZ[i][j] = (A)0;
 
   issue(0);
   for (int r = 0; r < nruns; ++r) {
@@ -360,25 +360,26 @@ project_tiled_kernel(const T* __restrict__ O, const T* __restrict__ G, int64_t l
     __syncthreads();
     if (active) {
       const int st = r & 1;
-      const T* os = Os + st * kTSp * kL + (4 * sg) * kL;
-      const T* gs = Gs + st * kTSp * kL + (4 * sg) * kL;
-      const A* ds = Ds + st * 32 * kL + (4 * dg) * kL;
+      const T* os = Os + st * kTSp * kL + (2 * sg) * kL;
+      const T* gs = Gs + st * kTSp * kL + (2 * sg) * kL;
+      const A* ds = Ds + st * 32 * kL + (DT * dg) * kL;
       const A* sh = Sh + st * kC;
       const int pc = min(kC, pb.m - r * kC);
-#pragma unroll 2
+#pragma unroll 4
       for (int c = 0; c < pc; ++c) {
         const A shc = sh[c];
-        A o[4], g[4], d[4];
+        A o[2], g[2], d[DT];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < 2; ++i) {
           o[i] = (A)os[i * kL + c] - shc;
           g[i] = (A)gs[i * kL + c];
-          d[i] = ds[i * kL + c];
         }
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < DT; ++j) d[j] = ds[j * kL + c];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int j = 0; j < DT; ++j) {
             accY[i][j] = fma(d[j], o[i], accY[i][j]);
             accZ[i][j] = fma(d[j], g[i], accZ[i][j]);
           }
@@ -388,12 +389,12 @@ project_tiled_kernel(const T* __restrict__ O, const T* __restrict__ G, int64_t l
   }
   if (!active) return;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int64_t s = s_base + 4 * sg + i;
+  for (int i = 0; i < 2; ++i) {
+    const int64_t s = s_base + 2 * sg + i;
     if (s >= ns) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int jj = 4 * dg + j;
+    for (int j = 0; j < DT; ++j) {
+      const int jj = DT * dg + j;
       if (jj >= pb.nd) continue;
       const int64_t oc = pb.oc + jj;
       A y = accY[i][j];
@@ -460,11 +461,18 @@ void launch_project(const T* O, const T* G, int64_t ldo, int64_t ldg, const doub
   using A = TO;   // FP64 path: FP64 throughout; mixed path: FP32 products and sums
   if (max_nd <= 32) {
     constexpr size_t smem_t = proj_tiled_smem<T, A>();
-    cudaFuncSetAttribute(project_tiled_kernel<T, A, TO>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
     dim3 grid((unsigned)((ns + kTSp - 1) / kTSp), (unsigned)nblocks);
-    project_tiled_kernel<T, A, TO><<<grid, kThreads, smem_t, st>>>(O, G, ldo, ldg, shift, shift32,
-                                                                    blocks, cen, Y, Z, ldout, ns);
+    if (max_nd <= 20) {
+      cudaFuncSetAttribute(project_tiled_kernel<T, A, TO, 5>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
+      project_tiled_kernel<T, A, TO, 5><<<grid, kThreads, smem_t, st>>>(
+          O, G, ldo, ldg, shift, shift32, blocks, cen, Y, Z, ldout, ns);
+    } else {
+      cudaFuncSetAttribute(project_tiled_kernel<T, A, TO, 8>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
+      project_tiled_kernel<T, A, TO, 8><<<grid, kThreads, smem_t, st>>>(
+          O, G, ldo, ldg, shift, shift32, blocks, cen, Y, Z, ldout, ns);
+    }
     return;
   }
   const size_t smem = sizeof(A) * (size_t)(2 * kPS * kPL + max_nd * kPL);
