@@ -40,6 +40,18 @@ def useful_flop_per_sample(wl):
     return pass1 + pass2
 
 
+def profiled_traffic(name):
+    """DRAM bytes per launch recorded from an ncu capture in profiles/<name> (a line
+    'traffic_bytes_per_launch: <bytes>'), or None."""
+    try:
+        for line in open(os.path.join(ROOT, "profiles", name)):
+            if line.strip().startswith("traffic_bytes_per_launch:"):
+                return float(line.split(":", 1)[1].split()[0])
+    except Exception:
+        pass
+    return None
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -180,35 +192,44 @@ def run_ours(args, rank, world):
                flop=flop, steps=args.steps)
     step.close()
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel (largest summed device time in the step)
     pk = peaks()
     kname, (kms, klaunch) = max(prof.items(), key=lambda kv: kv[1][0])
     res["dominant"] = kname
     roof = None
-    if kname in ("contract_tc_pass1", "contract_f64") and klaunch:
-        per_launch_bytes = 2 * (ns / klaunch) * n * O.element_size()
+    offs = wl.block_offsets
+    m = [offs[b + 1] - offs[b] for b in range(len(offs) - 1)]
+    # tcgen05 MACs per sample of the first sweep: 128 x 256 tiles over [O'_b | X'_b] x O'_b
+    tile_macs = sum(((mb + 127) // 128) * 2 * ((mb + 255) // 256) * 256 * 128 for mb in m)
+    ms1, l1 = prof.get("contract_tc_pass1", (0.0, 0))
+    if l1:
+        per_launch_samples = ns * res["steps"] / l1
+        exec_flop = 2 * 4 * tile_macs * per_launch_samples     # hi*hi + hi*lo + lo*hi + lo*lo
+        t_launch = ms1 / l1 / 1e3
+        res["tc_pass1"] = {"ms_per_launch": round(ms1 / l1, 3), "launches": l1,
+                           "hbm_gbs_algorithmic": round(2 * per_launch_samples * n * 4 / t_launch / 1e9, 1),
+                           "tensor_tflops_executed": round(exec_flop / t_launch / 1e12, 1),
+                           "useful_tflops": round(sum(3 * mb * mb for mb in m) * per_launch_samples / t_launch / 1e12, 1)}
+    if kname == "contract_tc_pass1" and l1:
+        p = pk.get("bf16_tflops_sustained", 1700.0)
+        ach = res["tc_pass1"]["tensor_tflops_executed"]
+        roof = {"bound": "tensor", "achieved": ach, "peak": p, "unit": "TFLOP/s",
+                "frac": round(ach / p, 4), "traffic": profiled_traffic("tc_accumulate_n16384.md"),
+                "kernel": "tc_accumulate_kernel (first sweep)",
+                "per_launch_algorithmic_flop": exec_flop,
+                "peak_source": "measured bf16 sustained" if "bf16_tflops_sustained" in pk else "fallback"}
+    elif kname == "contract_f64" and klaunch:
+        per_launch_bytes = 2 * (ns * res["steps"] / klaunch) * n * O.element_size()
         ach = per_launch_bytes / (kms / klaunch / 1e3) / 1e9
         p = pk.get("hbm_gbs", 6800.0)
         roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": p, "unit": "GB/s",
-                "frac": round(ach / p, 4), "traffic": None,
-                "kernel": kname, "per_launch_algorithmic_bytes": per_launch_bytes,
+                "frac": round(ach / p, 4), "traffic": None, "kernel": kname,
+                "per_launch_algorithmic_bytes": per_launch_bytes,
                 "peak_source": "measured" if "hbm_gbs" in pk else "fallback"}
     elif klaunch:
         roof = {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
                 "traffic": None, "kernel": kname,
-                "note": "dominant kernel is the FP64 eigen-solver (latency/FP64-ALU bound)"}
-    # tensor-core pass-1 kernel: always report its HBM roofline and executed tensor rate
-    ms1, l1 = prof.get("contract_tc_pass1", (0.0, 0))
-    if l1:
-        b1 = 2 * (ns / l1) * n * 4
-        offs = wl.block_offsets
-        m = [offs[b + 1] - offs[b] for b in range(len(offs) - 1)]
-        tiles_cols = sum(((mb + 127) // 128) * 2 * ((mb + 255) // 256) * 256 * 128 for mb in m)
-        exec_flop = 2 * 4 * tiles_cols * (ns / l1)
-        res["tc_pass1"] = {"ms_per_launch": kms and ms1 / l1, "launches": l1,
-                           "hbm_gbs": b1 / (ms1 / l1 / 1e3) / 1e9,
-                           "tensor_tflops_executed": exec_flop / (ms1 / l1 / 1e3) / 1e12,
-                           "useful_tflops": sum(3 * mb * mb for mb in m) * (ns / l1) / (ms1 / l1 / 1e3) / 1e12}
+                "note": "dominant kernel is the FP64 eigen-solver (FP64 latency / ALU bound)"}
     res["roofline"] = roof
     res["gpu_launches"] = int(sum(v[1] for v in prof.values()))
 

@@ -56,8 +56,9 @@ typedef enum {
 typedef enum {
   BLM_PREC_F64 = 0,    /* sample contractions in FP64 on CUDA cores                         */
   BLM_PREC_BF16X4 = 1, /* sample contractions on tcgen05 tensor cores: each operand split into
-                          bf16 hi + lo (2^-16 relative), four products accumulated in FP32
-                          (TMEM), promoted to FP64; centring and eigen-solves stay FP64       */
+                          bf16 hi + lo (2^-16 relative), the four products hi*hi + hi*lo +
+                          lo*hi + lo*lo accumulated in FP32 (TMEM), promoted to FP64;
+                          centring and eigen-solves stay FP64                                */
   BLM_PREC_TF32X3 = 2  /* as BF16X4 with a TF32 hi + FP32 lo split (2^-22 relative) and the
                           three products hi*hi + hi*lo + lo*hi on kind::tf32                 */
 } blm_precision;

@@ -271,7 +271,16 @@ __device__ bool hqr_windowed(R* G, int m, double* wr, double* wi, double anorm, 
   int its = 0, total = 0;
   const int limit = 40 * m + 100;
   auto g = [&](int i, int j) -> R& { return G[(int64_t)i * m + j]; };
+#ifdef BLM_EIG_TIMING
+  long long qt[4] = {0, 0, 0, 0}, qc = 0, nsweep = 0, nstep = 0;
+#define QR_T0() (qc = clock64())
+#define QR_T(i) (qt[i] += clock64() - qc, qc = clock64())
+#else
+#define QR_T0() ((void)0)
+#define QR_T(i) ((void)0)
+#endif
   while (hi >= 0) {
+    QR_T0();
     // --- deflation: the largest i in [1, hi] whose subdiagonal entry is negligible ---
     if (t == 0) sh.iscal[0] = 0;
     __syncthreads();
@@ -322,6 +331,10 @@ __device__ bool hqr_windowed(R* G, int m, double* wr, double* wi, double anorm, 
     if (total >= limit) return false;
     ++its;
     ++total;
+#ifdef BLM_EIG_TIMING
+    ++nsweep;
+    nstep += hi - l;
+#endif
     // --- shifts and the first column of the double-shift polynomial (thread 0) ---
     if (t == 0) {
       if (l > 0) g(l, l - 1) = zero;
@@ -344,6 +357,7 @@ __device__ bool hqr_windowed(R* G, int m, double* wr, double* wi, double anorm, 
       sh.scal[2] = to_double(z0);
     }
     __syncthreads();
+    QR_T(0);
     // --- the sweep, window by window ---
     for (int ks = l; ks <= hi - 1;) {
       const int ke = min(ks + kWin - 5, hi - 1);   // steps ks..ke in this window
@@ -355,6 +369,7 @@ __device__ bool hqr_windowed(R* G, int m, double* wr, double* wi, double anorm, 
         win[r * kWinLd + c] = g(a + r, a + c);
       }
       __syncthreads();
+      QR_T(1);
       if (t < kChase) {
         auto W = [&](int i, int j) -> R& { return win[(i - a) * kWinLd + (j - a)]; };
         for (int k = ks; k <= ke; ++k) {
@@ -426,6 +441,7 @@ __device__ bool hqr_windowed(R* G, int m, double* wr, double* wi, double anorm, 
         }
       }
       __syncthreads();
+      QR_T(2);
       for (int idx = t; idx < w * w; idx += nt) {
         const int r = idx / w, c = idx - r * w;
         g(a + r, a + c) = win[r * kWinLd + c];
@@ -465,9 +481,17 @@ __device__ bool hqr_windowed(R* G, int m, double* wr, double* wi, double anorm, 
         if (ke + 2 <= hi) G[base + (int64_t)(ke + 2) * step] = e1;
       }
       __syncthreads();
+      QR_T(3);
       ks = ke + 1;
     }
   }
+#ifdef BLM_EIG_TIMING
+  if (t == 0 && blockIdx.x == 0)
+    printf("qr m=%d sweeps %lld steps %lld: deflate+shift %lld window-load %lld chase %lld far %lld cycles\n",
+           m, nsweep, nstep, qt[0], qt[1], qt[2], qt[3]);
+#endif
+#undef QR_T0
+#undef QR_T
   return true;
 }
 

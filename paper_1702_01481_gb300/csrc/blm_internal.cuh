@@ -93,10 +93,12 @@ struct TcTile {
   double* out;
 };
 bool tc_supported();
+// Tensor-core contraction of one chunk (blm_sweep_tc.cu).  tiles_aligned: every tile's parameter
+// offsets are multiples of 4 (TMA staging allowed).
 cudaError_t launch_tc_accumulate(const float* Y, const float* Z, const float* E, const float* w,
-                                 int64_t ns, int64_t ld, const float* shift32,
-                                 const TcTile* tiles, int ntiles, int32_t* err, int tf32,
-                                 cudaStream_t st);
+                                 int64_t ns, int64_t ncols, int64_t ld, const float* shift32,
+                                 const TcTile* tiles, int ntiles, int tiles_aligned, int32_t* err,
+                                 int tf32, cudaStream_t st);
 
 // ------------------------------- launchers (blm_assemble.cu) ---------------------------------
 struct BlockAsm {

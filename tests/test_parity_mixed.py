@@ -123,6 +123,17 @@ def test_block_larger_than_tile(torch_cuda):
     check(got, ref, O, G, E, None, wl.block_offsets, wl.n_keep)
 
 
+def test_combined_sums_of_256_directions(torch_cuda):
+    """16 blocks of 32 with K = 16: the combined problem has 256 directions, so the second sweep's
+    contraction runs with full-width (TMA-staged) tiles as in the 16384-parameter step."""
+    wl = synth.Workload("t", 512, 4096, synth.equal_blocks(512, 16), 16, decades=4.0, chunk=4096,
+                        seed=8)
+    O, G, E = f32_inputs(wl)
+    ref = oracle_f32(O, G, E, None, wl.block_offsets, wl.n_keep)
+    got = run_mixed(torch_cuda, O, G, E, None, wl.block_offsets, wl.n_keep, chunks=[2048, 2048])
+    check(got, ref, O, G, E, None, wl.block_offsets, wl.n_keep)
+
+
 @pytest.mark.parametrize("which", ["n200", "blocks256"])
 def test_tf32_split_precision(torch_cuda, which):
     """The TF32 hi/lo split (2^-22 operand representation): same checks, with the matrix and
