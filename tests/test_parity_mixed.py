@@ -148,3 +148,16 @@ def test_tf32_split_precision(torch_cuda, which):
     ref = oracle_f32(O, G, E, None, wl.block_offsets, wl.n_keep)
     got = run_mixed(torch_cuda, O, G, E, None, wl.block_offsets, wl.n_keep, prec=blm.BLM_PREC_TF32X3)
     check(got, ref, O, G, E, None, wl.block_offsets, wl.n_keep)
+
+
+def test_uneven_blocks_full_parameter_count_tf32(torch_cuda):
+    """The uneven-block workload at its full shape (16384 parameters in 48 blocks of 64 - 640,
+    K = 16, TF32X3 contractions) on its first 2048 samples: block problems up to 617, a
+    769-direction combined problem (Davidson), unaligned block offsets (register-staged tiles)."""
+    import paper_1702_01481_gb300 as blm
+    wl = synth.workload("n16384u")
+    O, G, E = f32_inputs(wl, count=2048)
+    ref = oracle_f32(O, G, E, None, wl.block_offsets, wl.n_keep)
+    got = run_mixed(torch_cuda, O, G, E, None, wl.block_offsets, wl.n_keep, chunks=[2048],
+                    prec=blm.BLM_PREC_TF32X3)
+    check(got, ref, O, G, E, None, wl.block_offsets, wl.n_keep)
