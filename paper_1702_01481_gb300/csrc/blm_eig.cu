@@ -146,33 +146,50 @@ __device__ __forceinline__ double mag(double x) { return fabs(x); }
 __device__ __forceinline__ dw dw_abs(dw x) { return x.hi < 0.0f ? -x : x; }
 __device__ __forceinline__ dw dw_scale(dw x, float p2) { return dw{x.hi * p2, x.lo * p2}; }  // p2 = 2^k
 
+// 1/sqrt(a) and 1/a of a double word a (a > 0 for the square root, a in the normal FP32 range):
+// an FP32 seed r0 (2^-22 or better) and a Newton-Raphson step whose correction term
+// e = 1 - a r0^2 (or 1 - a r0) is small, so it needs FP32 precision only and is evaluated with
+// FMAs on the exact product r0^2.  That leaves 2^-46 for 1/x; 1/sqrt takes a second step in
+// double words (the first leaves about 2^-44).
+__device__ __forceinline__ dw dw_rsqrt(dw a) {
+  const float r0 = rsqrtf(a.hi);
+  const float p = __fmul_rn(r0, r0);
+  const float pl = __fmaf_rn(r0, r0, -p);                 // r0^2 = p + pl exactly
+  float e = __fmaf_rn(-a.hi, p, 1.0f);
+  e = __fmaf_rn(-a.hi, pl, e);
+  e = __fmaf_rn(-a.lo, p, e);
+  const dw r1 = dw_fast_two_sum(r0, __fmul_rn(0.5f * r0, e));
+  const dw e1 = dw_of(1.0f) - a * (r1 * r1);
+  return r1 + dw_scale(r1 * dw_of(e1.hi), 0.5f);
+}
+__device__ __forceinline__ dw dw_rcp(dw a) {
+  const float r0 = __frcp_rn(a.hi);
+  float e = __fmaf_rn(-a.hi, r0, 1.0f);
+  e = __fmaf_rn(-a.lo, r0, e);
+  return dw_fast_two_sum(r0, __fmul_rn(r0, e));
+}
+
 // Householder reflector of house3 in double words.  (x, y, z) is first scaled by a power of two
-// near 1 / max(|x|, |y|, |z|) so that no square under- or overflows FP32; 1/sqrt and 1/x use an
-// FP32 seed and two Newton-Raphson steps carried out in double words.
+// near 1 / max(|x|, |y|, |z|) so that no square under- or overflows FP32.
 __device__ void house3(dw x, dw y, dw z, dw& beta, dw& v1, dw& v2, dw& alpha) {
   const float amax = fmaxf(mag(x), fmaxf(mag(y), mag(z)));
-  if (mag(y) == 0.0f && mag(z) == 0.0f) {
+  if ((mag(y) == 0.0f && mag(z) == 0.0f) || !(amax >= 1e-30f)) {   // nothing to annihilate
     beta = v1 = v2 = dw_of(0.0f);
     alpha = x;
     return;
   }
-  int ex;
-  frexpf(amax, &ex);
-  const float f = ldexpf(1.0f, -ex), finv = ldexpf(1.0f, ex);
+  // power-of-two scale from the exponent field (amax is a normal FP32 number here)
+  const int ex = ((__float_as_int(amax) >> 23) & 0xff) - 127;
+  const float f = __int_as_float((127 - ex) << 23), finv = __int_as_float((127 + ex) << 23);
   x = dw_scale(x, f);
   y = dw_scale(y, f);
   z = dw_scale(z, f);
-  const dw n2 = x * x + (y * y + z * z);                 // in [1/4, 3]
-  dw rho = dw_of(rsqrtf(n2.hi));
-  for (int it = 0; it < 2; ++it) {
-    const dw e = dw_of(1.0f) - n2 * (rho * rho);
-    rho = rho + dw_scale(rho * e, 0.5f);
-  }
+  const dw n2 = x * x + (y * y + z * z);                 // in [1, 12)
+  const dw rho = dw_rsqrt(n2);
   const dw mu = n2 * rho;
   const bool neg = x.hi < 0.0f;
   const dw v0 = neg ? x - mu : x + mu;
-  dw r = dw_of(__frcp_rn(v0.hi));
-  for (int it = 0; it < 2; ++it) r = r + r * (dw_of(1.0f) - v0 * r);
+  const dw r = dw_rcp(v0);
   v1 = y * r;
   v2 = z * r;
   beta = dw_of(1.0f) + dw_abs(x) * rho;
