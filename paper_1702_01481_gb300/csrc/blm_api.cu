@@ -69,6 +69,10 @@ struct blm_handle {
   double* d_shift = nullptr;
   float* d_shift32 = nullptr;
   float* d_B32 = nullptr;                   // B^(b) rows in FP32 (mixed-path projection)
+  uint8_t* d_opA = nullptr;                 // prepared split-BF16 operands of a sub-chunk
+  uint8_t* d_opBS = nullptr;                //   (BF16X4 first sweep): Y', w Y', w X' rows
+  uint8_t* d_opBH = nullptr;
+  int64_t op_row_bytes = 0;                 //   bytes per parameter row (kSubChunk / 32 x 128)
   int64_t B_words = 0;                      // doubles in d_B
   double* d_colsum = nullptr;
   double* d_vec = nullptr;       // sO | sEO | sG  (3n)
@@ -133,12 +137,13 @@ namespace {
 
 enum ProfClass {
   PC_SHIFT = 0, PC_SUMS = 1, PC_CONTRACT = 2, PC_TC1 = 3, PC_HIST = 4, PC_ASSEMBLE = 5,
-  PC_EIG_BLOCKS = 6, PC_DIRS = 7, PC_PROJECT = 8, PC_TC2 = 9, PC_EIG_COMBINED = 10, PC_UPDATE = 11
+  PC_EIG_BLOCKS = 6, PC_DIRS = 7, PC_PROJECT = 8, PC_TC2 = 9, PC_EIG_COMBINED = 10, PC_UPDATE = 11,
+  PC_PREP = 12
 };
 const char* kProfNames[BLM_PROF_CLASSES] = {
     "reference_shift", "first_moments", "contract_f64", "contract_tc_pass1", "history_terms",
     "assemble", "eig_blocks", "directions", "project", "contract_tc_pass2", "eig_combined",
-    "update"};
+    "update", "operand_prep"};
 
 cudaEvent_t pool_event(blm_handle* h) {
   if (!h->ev_pool.empty()) {
@@ -367,6 +372,12 @@ void plan(blm_handle* h, Alloc& a) {
   a.add((void**)&h->d_evec, 8 * VOsz);
   a.add((void**)&h->d_B, 8 * BOsz);
   a.add((void**)&h->d_B32, 4 * BOsz);
+  if (h->prec == BLM_PREC_BF16X4 && h->in_type == BLM_IN_F32) {
+    h->op_row_bytes = kSubChunk / 32 * 128;
+    a.add((void**)&h->d_opA, h->op_row_bytes * n);
+    a.add((void**)&h->d_opBS, h->op_row_bytes * n);
+    a.add((void**)&h->d_opBH, h->op_row_bytes * n);
+  }
   a.add((void**)&h->d_status, 4 * (h->nb + 8));
   a.add((void**)&h->d_Cc, 8 * dc * 2 * dc);
   a.add((void**)&h->d_cvec, 8 * 3 * dc);
@@ -468,6 +479,23 @@ blm_status accumulate_dev(blm_handle* h, const T* O, const T* G, const T* E, con
                         pick_splits(h->ntileh, cnt, 512), st);
       }
     }
+  } else if (h->d_opA) {
+    // split-BF16: operands prepared once per element, then TMA + tensor cores
+    for (int64_t s0 = 0; s0 < ns; s0 += kSubChunk) {
+      const int64_t cnt = std::min(kSubChunk, ns - s0);
+      const float* Wp = w ? (const float*)w + s0 : nullptr;
+      {
+        Prof pr(h, PC_PREP);
+        launch_prep((const float*)O + s0 * ld, (const float*)G + s0 * ld, (const float*)E + s0, Wp,
+                    cnt, ld, h->n, h->d_shift32, h->d_opA, h->d_opBS, h->d_opBH, h->op_row_bytes,
+                    st);
+      }
+      Prof pr(h, PC_TC1);
+      cudaError_t e = launch_tc_prepared(h->d_opA, h->d_opBS, h->d_opBH, h->n, h->op_row_bytes,
+                                         cnt, h->d_tc1, h->ntc1, Wp != nullptr,
+                                         h->d_status + h->nb + 2, st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "launch_tc_prepared");
+    }
   } else {
     if (!tc_supported()) return fail(h, BLM_ERR_UNSUPPORTED, "tensor-core path not built");
     Prof pr(h, PC_TC1);
@@ -516,11 +544,26 @@ blm_status project_dev(blm_handle* h, const T* O, const T* G, const T* E, const 
         launch_sums<float>(PY, PZ, Es, ws, cnt, dc, dc, dc, nullptr, h->d_cvec, h->d_cvec + dc,
                            h->d_cvec + 2 * dc, nullptr, true, st);
       }
-      Prof pr(h, PC_TC2);
-      cudaError_t e = launch_tc_accumulate(PY, PZ, Es, ws, cnt, dc, dc, nullptr, h->d_tc2,
-                                           h->ntc2, h->tc2_aligned, h->d_status + h->nb + 2,
-                                           h->prec == BLM_PREC_TF32X3, st);
-      if (e != cudaSuccess) return cuda_fail(h, e, "launch_tc_accumulate (combined)");
+      if (h->d_opA && dc <= h->n) {
+        // split-BF16: the projections p (already centred) and r take the first sweep's route,
+        // prepared operands (no shift) then TMA + tensor cores
+        {
+          Prof pr(h, PC_PREP);
+          launch_prep(PY, PZ, Es, ws, cnt, dc, dc, nullptr, h->d_opA, h->d_opBS, h->d_opBH,
+                      h->op_row_bytes, st);
+        }
+        Prof pr(h, PC_TC2);
+        cudaError_t e = launch_tc_prepared(h->d_opA, h->d_opBS, h->d_opBH, dc, h->op_row_bytes,
+                                           cnt, h->d_tc2, h->ntc2, ws != nullptr,
+                                           h->d_status + h->nb + 2, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "launch_tc_prepared (combined)");
+      } else {
+        Prof pr(h, PC_TC2);
+        cudaError_t e = launch_tc_accumulate(PY, PZ, Es, ws, cnt, dc, dc, nullptr, h->d_tc2,
+                                             h->ntc2, h->tc2_aligned, h->d_status + h->nb + 2,
+                                             h->prec == BLM_PREC_TF32X3, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "launch_tc_accumulate (combined)");
+      }
     }
   }
   return BLM_OK;
@@ -873,10 +916,17 @@ blm_status blm_combined_solve(blm_handle* h, double* dmu, double* e_pred) {
   }
   {
     Prof pr(h, PC_EIG_COMBINED);
-    if (h->dc + 1 <= kDenseCombinedMax)
+    if (h->dc + 1 <= kDenseCombinedMax) {
       launch_eig(h->d_ceigp, 1, 512, st);
-    else
+    } else {
       launch_davidson(h->d_ceigp, 1, kDavidsonTol, kDavidsonIter, st);
+      // a Davidson run that did not converge (clustered or ill-conditioned combined problems
+      // from few samples) falls back to the dense solver on the same matrices
+      int32_t dstat = 0;
+      BLM_CU(h, cudaMemcpyAsync(&dstat, h->d_status + h->nb, 4, cudaMemcpyDeviceToHost, st));
+      BLM_CU(h, cudaStreamSynchronize(st));
+      if (dstat == ST_NOCONV) launch_eig(h->d_ceigp, 1, 512, st);
+    }
   }
   {
     Prof pr(h, PC_UPDATE, 2);

@@ -77,6 +77,12 @@ void launch_project(const T* O, const T* G, int64_t ldo, int64_t ldg, const doub
                     const float* shift32,
                     const ProjBlock* blocks, int nblocks, const double* cen, TO* Y, TO* Z,
                     int64_t ldout, int64_t ns, int max_m, int max_nd, cudaStream_t st);
+// Split-BF16 operands of a chunk of at most row_bytes / 4 samples (blm_prep.cu): rows of
+// row_bytes per parameter, 128 bytes per 32-sample group ([hi(32) | lo(32)] bf16).  opBS is
+// written only when w is given.
+void launch_prep(const float* O, const float* G, const float* E, const float* w, int64_t ns,
+                 int64_t ld, int64_t n, const float* shift32, uint8_t* opA, uint8_t* opBS,
+                 uint8_t* opBH, int64_t row_bytes, cudaStream_t st);
 // dst[i] = (float)src[i], i < count
 void launch_to_f32(const double* src, float* dst, int64_t count, cudaStream_t st);
 
@@ -92,6 +98,10 @@ struct TcTile {
   int32_t pad;
   double* out;
 };
+// Tensor-core contraction of prepared operands (blm_sweep_tc.cu, tc_op_kernel).
+cudaError_t launch_tc_prepared(const uint8_t* opA, const uint8_t* opBS, const uint8_t* opBH,
+                               int64_t nrows, int64_t row_bytes, int64_t ns, const TcTile* tiles,
+                               int ntiles, int weighted, int32_t* err, cudaStream_t st);
 bool tc_supported();
 // Tensor-core contraction of one chunk (blm_sweep_tc.cu).  tiles_aligned: every tile's parameter
 // offsets are multiples of 4 (TMA staging allowed).

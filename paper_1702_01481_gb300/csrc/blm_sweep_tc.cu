@@ -60,8 +60,8 @@ constexpr uint32_t kWaitLimit = 1u << 24;          // polls (each try_wait may s
 enum { A_VIEW = 0, A_FROM_B = 1, A_SEPARATE = 2 };
 
 struct Bars {
-  uint64_t op_full[kStages];
-  uint64_t op_empty[kStages];
+  uint64_t op_full[4];       // operand ring (kStages slots, four in tc_op_kernel)
+  uint64_t op_empty[4];
   uint64_t f_full[3];        // TMA-staged kernel: FP32 tile ring
   uint64_t f_empty[3];
   uint64_t l1_full;
@@ -670,14 +670,13 @@ __device__ __forceinline__ float lds_f1(uint32_t addr) {
 // X', weighted; A rows too in A_FROM_B mode); kind 1: separate A rows (Y').
 __device__ __forceinline__ void convert_job_tma(const Params& P, const TileInfo& ti, int kind,
                                                 int rowgroup, int sg, int64_t stage_base,
-                                                int64_t s_end, uint32_t ftile, uint32_t op) {
+                                                int64_t s_end, uint32_t ftile, uint32_t op,
+                                                float sh, float e_reg, float w_reg) {
   const int lane = threadIdx.x & 31;
   const bool xt = (kind == 0) && ti.xtype;
   const int r0 = (sg & 1) * 8;                   // first row of these samples in the tile
   const int row = rowgroup * 32 + lane;
   const bool vr = row < (kind == 0 ? ti.nB : ti.nA);
-  const int64_t par = ti.lo + (kind == 0 ? ti.pb : ti.row0) + row;
-  const float sh = (vr && P.shift) ? __ldg(P.shift + par) : 0.0f;
   const int rowlen = kind == 0 ? kBRows : kARows;
   const uint32_t ysrc = ftile + (kind == 0 ? 0u : (uint32_t)(2 * kFBoxB)) + (uint32_t)(row * 4);
   const uint32_t zsrc = ftile + (uint32_t)kFBoxB + (uint32_t)(row * 4);
@@ -692,8 +691,11 @@ __device__ __forceinline__ void convert_job_tma(const Params& P, const TileInfo&
   for (int q = 0; q < 8; ++q) {
     const int64_t s = stage_base + 8 * sg + q;
     const bool ok = vr && s < s_end;
-    const float e = (xt && ok) ? __ldg(P.E + s) : 0.0f;
-    const float wv = (kind == 0 && P.w && ok) ? __ldg(P.w + s) : 1.0f;
+    // E and w of the tile's 16 samples sit in lanes 0..15 (loaded once per tile)
+    const float e_s = __shfl_sync(0xffffffffu, e_reg, r0 + q);
+    const float w_s = __shfl_sync(0xffffffffu, w_reg, r0 + q);
+    const float e = (xt && ok) ? e_s : 0.0f;
+    const float wv = (kind == 0 && P.w && ok) ? w_s : 1.0f;
     yy[q] = ok ? y[q] - sh : 0.0f;
     x[q] = (xt ? fmaf(e, yy[q], z[q]) : yy[q]) * wv;
   }
@@ -850,6 +852,20 @@ tc_tma_kernel(const Params P, const __grid_constant__ CUtensorMap mapY,
       // jobs of one FP32 tile: (row group, sample group) over B rows, then separate A rows
       const int nb_rg = kBRows / 32, na_rg = (ti.amode == A_SEPARATE) ? kARows / 32 : 0;
       const int njobs = 2 * (nb_rg + na_rg);
+      // this warp's jobs j = cw + 10 i keep their rows for the whole unit: load their shifts once
+      float shv[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const int j = cw + kConvWarpsT * i;
+        shv[i] = 0.0f;
+        if (j < njobs && P.shift) {
+          const int jr = j >> 1;
+          const int kind = jr < nb_rg ? 0 : 1;
+          const int row = (kind ? jr - nb_rg : jr) * 32 + lane;
+          if (row < (kind ? ti.nA : ti.nB))
+            shv[i] = __ldg(P.shift + ti.lo + (kind ? ti.row0 : ti.pb) + row);
+        }
+      }
       for (int st = 0; st < nst; ++st, ++g) {
         const uint32_t slot = g % kStages, use = g / kStages;
         alive = mbar_wait(&bars->op_empty[slot], (use & 1) ^ 1, bars, P.err, 14);
@@ -859,14 +875,22 @@ tc_tma_kernel(const Params P, const __grid_constant__ CUtensorMap mapY,
         // each 16-sample tile is released as soon as every warp is done with it
         for (int half = 0; half < 2 && alive; ++half, ++f) {
           const uint32_t fslot = f % kFStages;
+          // E and w of this tile's samples (lanes 0..15), issued before the wait on the tile
+          const int64_t ys = base + 16 * half + (lane & 15);
+          const float e_reg = (ti.xtype && ys < sb) ? __ldg(P.E + ys) : 0.0f;
+          const float w_reg = (P.w && ys < sb) ? __ldg(P.w + ys) : 1.0f;
           alive = mbar_wait(&bars->f_full[fslot], (f / kFStages) & 1, bars, P.err, 16);
           if (!alive) break;
           const uint32_t ftile = fbase + fslot * (uint32_t)kFStageBytes;
-          for (int j = cw; j < njobs; j += kConvWarpsT) {
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            const int j = cw + kConvWarpsT * i;
+            if (j >= njobs) break;
             const int sg = 2 * half + (j & 1);
             const int jr = j >> 1;
             const int kind = jr < nb_rg ? 0 : 1;
-            convert_job_tma(P, ti, kind, kind ? jr - nb_rg : jr, sg, base, sb, ftile, op);
+            convert_job_tma(P, ti, kind, kind ? jr - nb_rg : jr, sg, base, sb, ftile, op, shv[i],
+                            e_reg, w_reg);
           }
           __syncwarp();
           if (lane == 0) mbar_arrive(&bars->f_empty[fslot]);
@@ -877,6 +901,147 @@ tc_tma_kernel(const Params P, const __grid_constant__ CUtensorMap mapY,
         if (lane == 0) mbar_arrive(&bars->op_full[slot]);
       }
     }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Prepared-operand variant (BF16X4): the operands were written to HBM once per sweep by the
+// preparation kernel (blm_prep.cu) in the tensor core's layout -- one 128-byte row per parameter
+// and 32-sample group holding [hi(32) | lo(32)] -- so this kernel only streams them: warp 1 loads
+// each stage's B rows (256 x 128 bytes) and, unless A is a view of B, its A rows (128 x 128
+// bytes) with 128-byte-swizzled cp.async.bulk.tensor into a four-deep ring; warp 0 issues the
+// four products of two K steps; warps 4-7 are the epilogue.  No converter warps.
+// ---------------------------------------------------------------------------------------------
+constexpr int kOpStagesP = 4;
+constexpr int kPStageBytes = (kBRows + kARows) * 128;          // 48 KB
+constexpr int kPBarOffset = kOpStagesP * kPStageBytes;          // 192 KB
+constexpr int kPSmemBytes = kPBarOffset + 256 + 1024;
+constexpr int kPThreads = 256;
+static_assert(kPSmemBytes <= 227 * 1024, "prepared-operand kernel exceeds shared memory");
+
+__global__ void __launch_bounds__(kPThreads, 1)
+tc_op_kernel(const Params P, const __grid_constant__ CUtensorMap mapA,
+             const __grid_constant__ CUtensorMap mapBS, const __grid_constant__ CUtensorMap mapBH) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  Bars* bars = (Bars*)(smem + kPBarOffset);
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kOpStagesP; ++s) {
+      mbar_init(&bars->op_full[s], 1);
+      mbar_init(&bars->op_empty[s], 1);
+    }
+    mbar_init(&bars->l1_full, 1);
+    mbar_init(&bars->l1_empty, 4);
+    mbar_init(&bars->drain, 1);
+    bars->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     smem_u32(&bars->tmem_base))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;
+  const int fs = P.flush_stages;
+
+  if (warp == 0) {
+    // ------------------------------- MMA issuer -------------------------------
+    uint32_t g = 0, k = 0;
+    bool alive = true;
+    for (int64_t u = blockIdx.x; u < P.nunits && alive; u += gridDim.x) {
+      const TileInfo ti = decode_tile(P.tiles[u % P.ntiles], P.w != nullptr);
+      const int64_t sa = (u / P.ntiles) * P.range_len;
+      const int64_t sb = min(P.ns, sa + P.range_len);
+      const int nst = (int)((sb - sa + kTmaStageK - 1) / kTmaStageK);
+      for (int st = 0; st < nst && alive; ++st, ++g) {
+        const uint32_t slot = g % kOpStagesP, use = g / kOpStagesP;
+        uint32_t acc = 1;
+        const bool istart = (st == 0) || ((st - 1) % fs == 0);
+        const bool iend = (st == 0) || ((st - 1) % fs == fs - 1) || (st == nst - 1);
+        if (istart) {
+          alive = mbar_wait(&bars->l1_empty, (k & 1) ^ 1, bars, P.err, 11);
+          tc_fence_after();
+          acc = (st == 0) ? 0 : 1;
+        }
+        if (alive) alive = mbar_wait(&bars->op_full[slot], use & 1, bars, P.err, 12);
+        if (!alive) break;
+        tc_fence_after();
+        if (lane == 0) {
+          const uint32_t ob = smem_u32(smem + slot * kPStageBytes);
+          const uint32_t oa = (ti.amode == A_VIEW) ? ob + (uint32_t)(ti.row0 - ti.pb) * 128u
+                                                   : ob + (uint32_t)kBRows * 128u;
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks) {
+            const uint32_t o = ks * 32;
+            mma_bf16(tmem, sdesc(oa + o), sdesc(ob + o), acc);           // hi * hi
+            mma_bf16(tmem, sdesc(oa + o), sdesc(ob + 64 + o), 1);        // hi * lo
+            mma_bf16(tmem, sdesc(oa + 64 + o), sdesc(ob + o), 1);        // lo * hi
+            mma_bf16(tmem, sdesc(oa + 64 + o), sdesc(ob + 64 + o), 1);   // lo * lo
+            acc = 1;
+          }
+          mma_commit(&bars->op_empty[slot]);
+          if (iend) mma_commit(&bars->l1_full);
+        }
+        __syncwarp();
+        if (iend) ++k;
+      }
+    }
+    if (lane == 0) mma_commit(&bars->drain);
+    __syncwarp();
+    for (uint32_t i = 0; i < kWaitLimit && !mbar_try_wait(&bars->drain, 0); ++i) {
+    }
+  } else if (warp == 1) {
+    // ------------------------------- TMA producer ------------------------------
+    uint32_t g = 0;
+    uint32_t armed[kOpStagesP] = {0, 0, 0, 0};
+    bool alive = true;
+    for (int64_t u = blockIdx.x; u < P.nunits && alive; u += gridDim.x) {
+      const TileInfo ti = decode_tile(P.tiles[u % P.ntiles], P.w != nullptr);
+      const int64_t sa = (u / P.ntiles) * P.range_len;
+      const int64_t sb = min(P.ns, sa + P.range_len);
+      const int nst = (int)((sb - sa + kTmaStageK - 1) / kTmaStageK);
+      const bool aview = ti.amode == A_VIEW;
+      const uint32_t bytes = (uint32_t)kBRows * 128u + (aview ? 0u : (uint32_t)kARows * 128u);
+      const CUtensorMap* mb = ti.xtype ? &mapBH : &mapBS;
+      for (int st = 0; st < nst && alive; ++st, ++g) {
+        const uint32_t slot = g % kOpStagesP, use = g / kOpStagesP;
+        alive = mbar_wait(&bars->op_empty[slot], (use & 1) ^ 1, bars, P.err, 15);
+        if (!alive) break;
+        if (lane == 0) {
+          uint64_t* bar = &bars->op_full[slot];
+          const uint32_t dst = smem_u32(smem + slot * kPStageBytes);
+          const int x = (int)((sa / kTmaStageK + st) * 64);
+          mbar_expect_tx(bar, bytes);
+          tma_load_2d(dst, mb, x, (int)(ti.lo + ti.pb), bar);
+          if (!aview) tma_load_2d(dst + kBRows * 128, &mapA, x, (int)(ti.lo + ti.row0), bar);
+        }
+        __syncwarp();
+        armed[slot] = use + 1;
+      }
+    }
+    for (int s = 0; s < kOpStagesP; ++s)
+      if (armed[s] > 0) {
+        for (uint32_t i = 0; i < kWaitLimit && !mbar_try_wait(&bars->op_full[s], (armed[s] - 1) & 1);
+             ++i) {
+        }
+      }
+  } else if (warp >= 4 && warp < 8) {
+    epilogue_role<kTmaStageK>(P, bars, tmem, warp, lane, fs);
   }
 
   tc_fence_before();
@@ -993,6 +1158,69 @@ cudaError_t launch_tc_accumulate(const float* Y, const float* Z, const float* E,
     tc_accumulate_kernel<true><<<grid, kThreads, kSmemBytes, st>>>(P);
   else
     tc_accumulate_kernel<false><<<grid, kThreads, kSmemBytes, st>>>(P);
+  return cudaGetLastError();
+}
+
+
+namespace {
+// 2-D tensor map over prepared bf16 operand rows: nrows x (row_bytes / 2) elements, boxes of
+// 64 elements (128 bytes) x box_rows rows, 128-byte swizzle (the layout tcgen05 reads K-major).
+bool encode_op_map(CUtensorMap* m, const uint8_t* base, int64_t nrows, int64_t row_bytes,
+                   int box_rows) {
+  EncodeTiledFn fn = encode_tiled_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)(row_bytes / 2), (cuuint64_t)nrows};
+  cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
+  cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint8_t*>(base), dims, strides,
+            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+}  // namespace
+
+cudaError_t launch_tc_prepared(const uint8_t* opA, const uint8_t* opBS, const uint8_t* opBH,
+                               int64_t nrows, int64_t row_bytes, int64_t ns, const TcTile* tiles,
+                               int ntiles, int weighted, int32_t* err, cudaStream_t st) {
+  if (ns <= 0 || ntiles <= 0) return cudaSuccess;
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(tc_op_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPSmemBytes);
+  }
+  CUtensorMap mA, mBS, mBH;
+  if (!encode_op_map(&mA, opA, nrows, row_bytes, kARows) ||
+      !encode_op_map(&mBS, weighted ? opBS : opA, nrows, row_bytes, kBRows) ||
+      !encode_op_map(&mBH, opBH, nrows, row_bytes, kBRows))
+    return cudaErrorInvalidValue;
+  Params P;
+  P.Y = nullptr;
+  P.Z = nullptr;
+  P.E = nullptr;
+  // decode_tile takes A as a view of B only without weights; the pointer is not dereferenced
+  P.w = weighted ? reinterpret_cast<const float*>(opBS) : nullptr;
+  P.shift = nullptr;
+  P.ns = ns;
+  P.ld = 0;
+  P.tiles = tiles;
+  P.ntiles = ntiles;
+  int64_t range = 8192;
+  while (range > kTmaStageK && ((ns + range - 1) / range) * ntiles < 8LL * sms) range /= 2;
+  P.range_len = range;
+  P.nunits = ((ns + range - 1) / range) * ntiles;
+  static int flush = -1;
+  if (flush < 0) {
+    const char* env = getenv("BLM_TC_FLUSH_SAMPLES");
+    flush = env ? atoi(env) : 128;
+    if (flush < 32) flush = 32;
+  }
+  P.flush_stages = flush / kTmaStageK > 0 ? flush / kTmaStageK : 1;
+  P.err = err;
+  P.vec_ok = 0;
+  const int grid = (int)(P.nunits < sms ? P.nunits : sms);
+  tc_op_kernel<<<grid, kPThreads, kPSmemBytes, st>>>(P, mA, mBS, mBH);
   return cudaGetLastError();
 }
 
