@@ -445,7 +445,8 @@ blm_status accumulate_dev(blm_handle* h, const T* O, const T* G, const T* E, con
     h->shift_set = true;
   }
   const bool mixed = h->prec != BLM_PREC_F64;
-  {
+  const bool prepared = mixed && h->d_opA != nullptr;   // first moments fused into the prep pass
+  if (!prepared) {
     Prof pr(h, PC_SUMS);
     launch_sums<T>(O, G, E, w, ns, ld, ld, h->n, h->d_shift, h->d_vec, h->d_vec + h->n,
                    h->d_vec + 2 * h->n, h->d_scal, mixed, st);
@@ -488,7 +489,7 @@ blm_status accumulate_dev(blm_handle* h, const T* O, const T* G, const T* E, con
         Prof pr(h, PC_PREP);
         launch_prep((const float*)O + s0 * ld, (const float*)G + s0 * ld, (const float*)E + s0, Wp,
                     cnt, ld, h->n, h->d_shift32, h->d_opA, h->d_opBS, h->d_opBH, h->op_row_bytes,
-                    st);
+                    h->d_vec, h->d_vec + h->n, h->d_vec + 2 * h->n, h->d_scal, st);
       }
       Prof pr(h, PC_TC1);
       cudaError_t e = launch_tc_prepared(h->d_opA, h->d_opBS, h->d_opBH, h->n, h->op_row_bytes,
@@ -537,20 +538,22 @@ blm_status project_dev(blm_handle* h, const T* O, const T* G, const T* E, const 
     } else {
       float* PY = (float*)h->d_scrY;
       float* PZ = (float*)h->d_scrZ;
+      const bool prepared = h->d_opA && dc <= h->n;
       {
-        Prof pr(h, PC_PROJECT, 2);
+        Prof pr(h, PC_PROJECT, prepared ? 1 : 2);
         launch_project<float, float>(Os, Gs, ld, ld, h->d_shift, h->d_shift32, h->d_pbB, h->nb, h->d_cen, PY,
                                      PZ, dc, cnt, h->maxM, h->maxK, st);
-        launch_sums<float>(PY, PZ, Es, ws, cnt, dc, dc, dc, nullptr, h->d_cvec, h->d_cvec + dc,
-                           h->d_cvec + 2 * dc, nullptr, true, st);
+        if (!prepared)
+          launch_sums<float>(PY, PZ, Es, ws, cnt, dc, dc, dc, nullptr, h->d_cvec, h->d_cvec + dc,
+                             h->d_cvec + 2 * dc, nullptr, true, st);
       }
-      if (h->d_opA && dc <= h->n) {
+      if (prepared) {
         // split-BF16: the projections p (already centred) and r take the first sweep's route,
         // prepared operands (no shift) then TMA + tensor cores
         {
           Prof pr(h, PC_PREP);
           launch_prep(PY, PZ, Es, ws, cnt, dc, dc, nullptr, h->d_opA, h->d_opBS, h->d_opBH,
-                      h->op_row_bytes, st);
+                      h->op_row_bytes, h->d_cvec, h->d_cvec + dc, h->d_cvec + 2 * dc, nullptr, st);
         }
         Prof pr(h, PC_TC2);
         cudaError_t e = launch_tc_prepared(h->d_opA, h->d_opBS, h->d_opBH, dc, h->op_row_bytes,

@@ -1241,7 +1241,17 @@ davidson_kernel(const EigProblem* __restrict__ probs, double tol, int max_iter) 
   bool fresh = true;      // projected matrix must be rebuilt (start, restart)
   double theta = 0.0;
   int status = ST_NOCONV;
+#ifdef BLM_EIG_TIMING
+  long long dt[5] = {0, 0, 0, 0, 0}, dc0 = clock64();
+  int dits = 0;
+#define DAV_T(i) (dt[i] += clock64() - dc0, dc0 = clock64())
+#else
+#define DAV_T(i) ((void)0)
+#endif
   for (int it = 0; it < max_iter; ++it) {
+#ifdef BLM_EIG_TIMING
+    dits = it + 1;
+#endif
     // projected matrix: only the newest row and column change between restarts
     for (int i = 0; i < k; ++i) {
       const bool newer = (i == k - 1);
@@ -1260,9 +1270,11 @@ davidson_kernel(const EigProblem* __restrict__ probs, double tol, int max_iter) 
     }
     if (t == 0) *sStat = ST_OK;
     __syncthreads();
+    DAV_T(0);
     EigProblem sp{k, 1, 0, 0, sS, sH, sW, sLam, sVec, sStat};
     dense_geig(sp, dsm, sh);
     __syncthreads();
+    DAV_T(1);
     if (*sStat != ST_OK) {
       status = *sStat;
       break;
@@ -1285,6 +1297,7 @@ davidson_kernel(const EigProblem* __restrict__ probs, double tol, int max_iter) 
     __syncthreads();
     const double rn = sqrt(dotv(r, r, m, sh));
     const double sn = sqrt(dotv(Su, Su, m, sh));
+    DAV_T(2);
     if (rn <= tol * sn * fmax(1.0, fabs(theta))) {
       status = ST_OK;
       break;
@@ -1316,6 +1329,7 @@ davidson_kernel(const EigProblem* __restrict__ probs, double tol, int max_iter) 
         __syncthreads();
       }
     double* stv = SV + (int64_t)k * m;
+    DAV_T(3);
     matvec(pb.S, m, tv, stv);
     const double nn = dotv(tv, stv, m, sh);
     if (!(nn > 1e-300)) {
@@ -1329,8 +1343,15 @@ davidson_kernel(const EigProblem* __restrict__ probs, double tol, int max_iter) 
     }
     __syncthreads();
     matvec(pb.H, m, tv, HV + (int64_t)k * m);
+    DAV_T(4);
     ++k;
   }
+#ifdef BLM_EIG_TIMING
+  if (t == 0)
+    printf("davidson m=%d iterations %d: projected %lld small-eig %lld ritz %lld correction %lld matvec %lld cycles\n",
+           m, dits, dt[0], dt[1], dt[2], dt[3], dt[4]);
+#endif
+#undef DAV_T
   if (t == 0) {
     *pb.status = status;
     pb.lam[0] = theta;

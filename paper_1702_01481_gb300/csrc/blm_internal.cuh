@@ -79,10 +79,12 @@ void launch_project(const T* O, const T* G, int64_t ldo, int64_t ldg, const doub
                     int64_t ldout, int64_t ns, int max_m, int max_nd, cudaStream_t st);
 // Split-BF16 operands of a chunk of at most row_bytes / 4 samples (blm_prep.cu): rows of
 // row_bytes per parameter, 128 bytes per 32-sample group ([hi(32) | lo(32)] bf16).  opBS is
-// written only when w is given.
-void launch_prep(const float* O, const float* G, const float* E, const float* w, int64_t ns,
+// written only when w is given.  With sY non-null the same pass adds the first moments
+// sum w Y', sum w E Y', sum w Z into sY, sEY, sZ (and sum w, sum w E into scal if non-null).
+void launch_prep(const float* Y, const float* Z, const float* E, const float* w, int64_t ns,
                  int64_t ld, int64_t n, const float* shift32, uint8_t* opA, uint8_t* opBS,
-                 uint8_t* opBH, int64_t row_bytes, cudaStream_t st);
+                 uint8_t* opBH, int64_t row_bytes, double* sY, double* sEY, double* sZ,
+                 double* scal, cudaStream_t st);
 // dst[i] = (float)src[i], i < count
 void launch_to_f32(const double* src, float* dst, int64_t count, cudaStream_t st);
 

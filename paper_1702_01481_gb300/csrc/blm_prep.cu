@@ -1,15 +1,21 @@
-// Operand preparation for the split-BF16 first sweep (Eq. 3 / Eq. 5 sums on tensor cores).
+// Operand preparation for the split-BF16 sweeps (Eq. 3 / Eq. 5 / Eq. 7 sums on tensor cores),
+// fused with the first-moment sums of the same sweep.
 //
 // Each FP32 sample element is converted once per sweep into the operands of the tensor-core
 // contraction, stored in HBM in the layout the tensor core reads (K-major, one 128-byte row per
 // parameter and 32-sample group: [hi(32 samples) | lo(32 samples)] in bf16):
-//   opA  = Y' = O - c                       (A operand, all tiles)
-//   opBH = w (E Y' + G)                     (B operand of the Hamiltonian tiles, X')
+//   opA  = Y' = Y - c                       (A operand, all tiles)
+//   opBH = w (E Y' + Z)                     (B operand of the Hamiltonian tiles, X')
 //   opBS = w Y'                             (B operand of the overlap tiles when weighted;
 //                                            without weights those tiles read opA)
-// so that the contraction kernel is TMA + MMA only.  A CTA takes 64 parameters x 64 samples:
-// coalesced FP32 loads of the sample rows into shared memory, then one thread per (parameter,
-// 32-sample group) reads its column, splits and writes its three 128-byte rows.
+// so that the contraction kernel is TMA + MMA only.  The same pass accumulates the first moments
+// sum w Y', sum w E Y', sum w Z per parameter (and sum w, sum w E) into FP64, in FP32 runs of 64
+// samples per thread and parameter.
+//
+// A CTA takes 64 parameters x 1024 samples in tiles of 64 samples, double-buffered through
+// shared memory by cp.async; thread (p4, sb) owns parameters 4 p4 .. 4 p4 + 3 and samples
+// 8 sb .. 8 sb + 7 of a tile: 16-byte shared-memory reads along the parameters, one 16-byte
+// store per parameter for hi and one for lo.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -20,11 +26,14 @@ namespace blm {
 
 namespace {
 
-constexpr int kPrepP = 64;            // parameters per CTA
-constexpr int kPrepS = 64;            // samples per CTA (2 groups of 32)
-constexpr int kPrepThreads = 128;     // one thread per (parameter, group)
-constexpr int kPrepLd = kPrepP + 4;   // padded smem row (16-byte aligned): a warp's
-                                      // column reads (32 parameters) hit different banks
+constexpr int kPrepP = 64;             // parameters per CTA
+constexpr int kPrepT = 64;             // samples per tile (two 32-sample groups)
+constexpr int kPrepTiles = 16;         // tiles per CTA
+constexpr int kPrepThreads = 128;      // 16 parameter quads x 8 sample blocks
+constexpr int kPrepLd = kPrepP + 4;    // padded row (16-byte aligned)
+constexpr int kPrepRun = 8;            // tiles per FP32 run of the sums (64 samples per thread)
+constexpr int kPrepBufFloats = 2 * kPrepT * kPrepLd + 2 * kPrepT;   // O, G, E, W of one tile
+constexpr size_t kPrepSmem = 2 * kPrepBufFloats * sizeof(float);
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float first, float second) {
   uint32_t d;
@@ -59,94 +68,211 @@ __device__ __forceinline__ void cp_async16(float* dst, const float* src, int byt
                : "memory");
 }
 
+struct PrepArgs {
+  const float* Y;
+  const float* Z;
+  const float* E;
+  const float* w;
+  int64_t ns, ld, n;
+  const float* shift;     // per-parameter c, or nullptr
+  uint8_t* opA;
+  uint8_t* opBS;          // nullptr without weights
+  uint8_t* opBH;
+  int64_t row_bytes;
+  double* sY;             // first moments (FP64 sums), or nullptr
+  double* sEY;
+  double* sZ;
+  double* scal;           // sum w, sum w E (CTAs of the first parameter tile), or nullptr
+  int vec;                // 16-byte copies allowed
+};
+
 __global__ void __launch_bounds__(kPrepThreads)
-prep_kernel(const float* __restrict__ O, const float* __restrict__ G,
-            const float* __restrict__ E, const float* __restrict__ w, int64_t ns, int64_t ld,
-            int64_t n, const float* __restrict__ shift, uint8_t* __restrict__ opA,
-            uint8_t* __restrict__ opBS, uint8_t* __restrict__ opBH, int64_t row_bytes) {
-  __shared__ __align__(16) float Os[kPrepS * kPrepLd];
-  __shared__ __align__(16) float Gs[kPrepS * kPrepLd];
-  __shared__ float Es[kPrepS], Ws[kPrepS];
+prep_kernel(const PrepArgs a) {
+  extern __shared__ __align__(16) float sm[];
   const int t = threadIdx.x;
+  const int p4 = t & 15, sb = t >> 4;
   const int64_t p0 = (int64_t)blockIdx.x * kPrepP;
-  const int64_t s0 = (int64_t)blockIdx.y * kPrepS;
-  // the whole tile in flight at once (cp.async, zero-filled outside the sample and parameter
-  // ranges): 16-byte copies when rows and the tile start are 16-byte aligned
-  const bool vec = (ld % 4 == 0) && ((((uintptr_t)O) | ((uintptr_t)G)) % 16 == 0);
-  if (vec) {
+  const int64_t sbase = (int64_t)blockIdx.y * kPrepT * kPrepTiles;
+  const int ntiles = (int)min((int64_t)kPrepTiles, (a.ns - sbase + kPrepT - 1) / kPrepT);
+
+  auto issue = [&](int ti) {
+    float* buf = sm + (ti & 1) * kPrepBufFloats;
+    float* Os = buf;
+    float* Gs = Os + kPrepT * kPrepLd;
+    float* Es = Gs + kPrepT * kPrepLd;
+    const int64_t s0 = sbase + (int64_t)ti * kPrepT;
+    if (a.vec) {
 #pragma unroll
-    for (int i = 0; i < kPrepS * kPrepP / 4 / kPrepThreads; ++i) {
-      const int idx = t + i * kPrepThreads;          // float4 index in the tile
-      const int s = idx / (kPrepP / 4), q = idx % (kPrepP / 4);
-      const int64_t p = p0 + 4 * q;
-      const bool srow = s0 + s < ns;
-      const int valid = (int)(srow ? max((int64_t)0, min((int64_t)4, n - p)) : 0);
-      const int64_t off = srow && valid ? (s0 + s) * ld + p : 0;
-      cp_async16(Os + s * kPrepLd + 4 * q, O + off, 4 * valid);
-      cp_async16(Gs + s * kPrepLd + 4 * q, G + off, 4 * valid);
-    }
-  } else {
+      for (int i = 0; i < kPrepT * kPrepP / 4 / kPrepThreads; ++i) {
+        const int idx = t + i * kPrepThreads;
+        const int s = idx >> 4, q = idx & 15;
+        const int64_t p = p0 + 4 * q;
+        const bool srow = s0 + s < a.ns;
+        const int valid = (int)(srow ? max((int64_t)0, min((int64_t)4, a.n - p)) : 0);
+        const int64_t off = valid ? (s0 + s) * a.ld + p : 0;
+        cp_async16(Os + s * kPrepLd + 4 * q, a.Y + off, 4 * valid);
+        cp_async16(Gs + s * kPrepLd + 4 * q, a.Z + off, 4 * valid);
+      }
+    } else {
 #pragma unroll 8
-    for (int i = 0; i < kPrepS * kPrepP / kPrepThreads; ++i) {
-      const int idx = t + i * kPrepThreads;
-      const int s = idx / kPrepP, p = idx % kPrepP;
-      const bool ok = (s0 + s < ns) && (p0 + p < n);
-      const int64_t off = ok ? (s0 + s) * ld + p0 + p : 0;
-      cp_async4(Os + s * kPrepLd + p, O + off, ok);
-      cp_async4(Gs + s * kPrepLd + p, G + off, ok);
+      for (int i = 0; i < kPrepT * kPrepP / kPrepThreads; ++i) {
+        const int idx = t + i * kPrepThreads;
+        const int s = idx / kPrepP, p = idx % kPrepP;
+        const bool ok = (s0 + s < a.ns) && (p0 + p < a.n);
+        const int64_t off = ok ? (s0 + s) * a.ld + p0 + p : 0;
+        cp_async4(Os + s * kPrepLd + p, a.Y + off, ok);
+        cp_async4(Gs + s * kPrepLd + p, a.Z + off, ok);
+      }
     }
-  }
-  asm volatile("cp.async.commit_group;" ::: "memory");
-  if (t < kPrepS) {
-    const bool ok = s0 + t < ns;
-    Es[t] = ok ? __ldg(E + s0 + t) : 0.0f;
-    Ws[t] = (ok && w) ? __ldg(w + s0 + t) : (ok ? 1.0f : 0.0f);
-  }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
-  __syncthreads();
-  const int p = t % kPrepP, gq = t / kPrepP;     // parameter, 32-sample group
-  const int64_t pg = p0 + p;
-  if (pg >= n) return;
-  const float c = shift ? __ldg(shift + pg) : 0.0f;
-  const int64_t grp = s0 / 32 + gq;              // sample group within the chunk
-  const int64_t rowoff = pg * row_bytes + grp * 128;
+    if (t < kPrepT) {
+      const bool ok = s0 + t < a.ns;
+      cp_async4(Es + t, a.E + (ok ? s0 + t : 0), ok);
+      if (a.w) cp_async4(Es + kPrepT + t, a.w + (ok ? s0 + t : 0), ok);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+
+  float c[4];
 #pragma unroll
-  for (int jb = 0; jb < 4; ++jb) {
-    float ya[8], xb[8], yb[8];
+  for (int e = 0; e < 4; ++e) {
+    const int64_t p = p0 + 4 * p4 + e;
+    c[e] = (a.shift && p < a.n) ? __ldg(a.shift + p) : 0.0f;
+  }
+  double dY[4] = {0, 0, 0, 0}, dEY[4] = {0, 0, 0, 0}, dZ[4] = {0, 0, 0, 0};
+  float fY[4] = {0, 0, 0, 0}, fEY[4] = {0, 0, 0, 0}, fZ[4] = {0, 0, 0, 0};
+  double dW = 0.0, dWE = 0.0;
+  const bool scal_thread = a.scal && blockIdx.x == 0 && p4 == 0;
+
+  issue(0);
+  for (int ti = 0; ti < ntiles; ++ti) {
+    if (ti + 1 < ntiles) {
+      issue(ti + 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+    const float* buf = sm + (ti & 1) * kPrepBufFloats;
+    const float* Os = buf;
+    const float* Gs = Os + kPrepT * kPrepLd;
+    const float* Es = Gs + kPrepT * kPrepLd;
+    const int64_t s0 = sbase + (int64_t)ti * kPrepT;
+    float ya[4][8], xb[4][8], yb[4][8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const int s = 32 * gq + 8 * jb + j;
-      const bool ok = s0 + s < ns;
-      const float y = ok ? Os[s * kPrepLd + p] - c : 0.0f;
-      const float wv = Ws[s];
-      ya[j] = y;
-      xb[j] = wv * fmaf(Es[s], y, Gs[s * kPrepLd + p]);
-      yb[j] = wv * y;
+      const int s = 8 * sb + j;
+      const bool ok = s0 + s < a.ns;
+      const float4 o = *reinterpret_cast<const float4*>(Os + s * kPrepLd + 4 * p4);
+      const float4 g = *reinterpret_cast<const float4*>(Gs + s * kPrepLd + 4 * p4);
+      const float ev = Es[s];
+      const float wv = ok ? (a.w ? Es[kPrepT + s] : 1.0f) : 0.0f;
+      if (scal_thread && sb >= 0) {
+        dW += (double)wv;
+        dWE += (double)(wv * ev);
+      }
+      const float ov[4] = {o.x, o.y, o.z, o.w}, gv[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float y = ok ? ov[e] - c[e] : 0.0f;
+        const float wy = wv * y;
+        ya[e][j] = y;
+        yb[e][j] = wy;
+        xb[e][j] = wv * fmaf(ev, y, gv[e]);
+        fY[e] += wy;
+        fEY[e] = fmaf(wy, ev, fEY[e]);
+        fZ[e] = fmaf(wv, gv[e], fZ[e]);
+      }
     }
-    uint4 hi, lo;
-    split8_bf16(ya, hi, lo);
-    *reinterpret_cast<uint4*>(opA + rowoff + 16 * jb) = hi;
-    *reinterpret_cast<uint4*>(opA + rowoff + 64 + 16 * jb) = lo;
-    split8_bf16(xb, hi, lo);
-    *reinterpret_cast<uint4*>(opBH + rowoff + 16 * jb) = hi;
-    *reinterpret_cast<uint4*>(opBH + rowoff + 64 + 16 * jb) = lo;
-    if (opBS) {
-      split8_bf16(yb, hi, lo);
-      *reinterpret_cast<uint4*>(opBS + rowoff + 16 * jb) = hi;
-      *reinterpret_cast<uint4*>(opBS + rowoff + 64 + 16 * jb) = lo;
+    const int64_t grp = s0 / 32 + (sb >> 2);
+    const int chunk = sb & 3;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int64_t p = p0 + 4 * p4 + e;
+      if (p >= a.n) continue;
+      const int64_t off = p * a.row_bytes + grp * 128 + 16 * chunk;
+      uint4 hi, lo;
+      split8_bf16(ya[e], hi, lo);
+      *reinterpret_cast<uint4*>(a.opA + off) = hi;
+      *reinterpret_cast<uint4*>(a.opA + off + 64) = lo;
+      split8_bf16(xb[e], hi, lo);
+      *reinterpret_cast<uint4*>(a.opBH + off) = hi;
+      *reinterpret_cast<uint4*>(a.opBH + off + 64) = lo;
+      if (a.opBS) {
+        split8_bf16(yb[e], hi, lo);
+        *reinterpret_cast<uint4*>(a.opBS + off) = hi;
+        *reinterpret_cast<uint4*>(a.opBS + off + 64) = lo;
+      }
     }
+    if ((ti + 1) % kPrepRun == 0 || ti + 1 == ntiles) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        dY[e] += (double)fY[e];
+        dEY[e] += (double)fEY[e];
+        dZ[e] += (double)fZ[e];
+        fY[e] = fEY[e] = fZ[e] = 0.0f;
+      }
+    }
+    __syncthreads();
+  }
+  if (a.sY) {
+    // the 8 sample blocks of a parameter quad: lanes p4 and p4 + 16 of a warp, then the 4 warps
+    double* red = reinterpret_cast<double*>(sm);   // tile buffers are free now
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      dY[e] += __shfl_xor_sync(0xffffffffu, dY[e], 16);
+      dEY[e] += __shfl_xor_sync(0xffffffffu, dEY[e], 16);
+      dZ[e] += __shfl_xor_sync(0xffffffffu, dZ[e], 16);
+    }
+    const int wid = t >> 5, lane = t & 31;
+    if (lane < 16) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        red[((wid * 16 + lane) * 4 + e) * 3 + 0] = dY[e];
+        red[((wid * 16 + lane) * 4 + e) * 3 + 1] = dEY[e];
+        red[((wid * 16 + lane) * 4 + e) * 3 + 2] = dZ[e];
+      }
+    }
+    __syncthreads();
+    if (t < kPrepP) {
+      const int q = t >> 2, e = t & 3;
+      const int64_t p = p0 + t;
+      double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      for (int w4 = 0; w4 < kPrepThreads / 32; ++w4) {
+        s1 += red[((w4 * 16 + q) * 4 + e) * 3 + 0];
+        s2 += red[((w4 * 16 + q) * 4 + e) * 3 + 1];
+        s3 += red[((w4 * 16 + q) * 4 + e) * 3 + 2];
+      }
+      if (p < a.n) {
+        atomicAdd(a.sY + p, s1);
+        atomicAdd(a.sEY + p, s2);
+        atomicAdd(a.sZ + p, s3);
+      }
+    }
+  }
+  if (scal_thread) {
+    atomicAdd(a.scal + 0, dW);
+    atomicAdd(a.scal + 1, dWE);
   }
 }
 
 }  // namespace
 
-void launch_prep(const float* O, const float* G, const float* E, const float* w, int64_t ns,
+void launch_prep(const float* Y, const float* Z, const float* E, const float* w, int64_t ns,
                  int64_t ld, int64_t n, const float* shift32, uint8_t* opA, uint8_t* opBS,
-                 uint8_t* opBH, int64_t row_bytes, cudaStream_t st) {
+                 uint8_t* opBH, int64_t row_bytes, double* sY, double* sEY, double* sZ,
+                 double* scal, cudaStream_t st) {
   if (ns <= 0) return;
-  dim3 grid((unsigned)((n + kPrepP - 1) / kPrepP), (unsigned)((ns + kPrepS - 1) / kPrepS));
-  prep_kernel<<<grid, kPrepThreads, 0, st>>>(O, G, E, w, ns, ld, n, shift32, opA,
-                                             w ? opBS : nullptr, opBH, row_bytes);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPrepSmem);
+    attr = true;
+  }
+  PrepArgs a{Y, Z, E, w, ns, ld, n, shift32, opA, w ? opBS : nullptr, opBH, row_bytes,
+             sY, sEY, sZ, scal,
+             (ld % 4 == 0) && ((((uintptr_t)Y) | ((uintptr_t)Z)) % 16 == 0) ? 1 : 0};
+  dim3 grid((unsigned)((n + kPrepP - 1) / kPrepP),
+            (unsigned)((ns + kPrepT * kPrepTiles - 1) / (kPrepT * kPrepTiles)));
+  prep_kernel<<<grid, kPrepThreads, kPrepSmem, st>>>(a);
 }
 
 }  // namespace blm
