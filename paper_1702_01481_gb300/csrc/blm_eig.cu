@@ -246,9 +246,9 @@ struct Shared {
 // sweep in the same order; the bulge column is set to (alpha, 0, 0) exactly.
 // Returns false if the iteration budget (40 m sweeps) runs out.
 // ---------------------------------------------------------------------------------------------
-constexpr int kWin = 64;
+constexpr int kWin = 128;
 constexpr int kWinLd = kWin + 1;
-constexpr int kChase = 64;
+constexpr int kChase = 128;
 
 __device__ __forceinline__ void chase_sync() {
   if (kChase == 32) {
@@ -564,7 +564,7 @@ __device__ void warp_hess_lu(const double* Hh, int m, double s_re, double s_im, 
       b = tmp;
     }
     if (cabs2(a) == 0.0) a = cmk(pert, 0.0);
-    const cplx lm = CX ? cdiv(b, a) : cmk(b.re / a.re, 0.0);
+    const cplx lm = CX ? cdiv(b, a) : cmk(b.re * rcp_nr(a.re), 0.0);
     __syncwarp();   // every lane has read row k before it is overwritten
     double* urk = U + urow(k, m) - k;
     for (int j = k + lane; j < m; j += 32) {
@@ -635,7 +635,7 @@ __device__ void warp_hess_solve(int m, double pert, const double* U, const doubl
       cplx d = cmk(urk[k], CX ? urk[half + k] : 0.0);
       if (cabs2(d) == 0.0) d = cmk(pert, 0.0);
       const cplx num = cmk(y[k] - sr, CX ? y[m + k] - si : 0.0);
-      const cplx x = CX ? cdiv(num, d) : cmk(num.re / d.re, 0.0);
+      const cplx x = CX ? cdiv(num, d) : cmk(num.re * rcp_nr(d.re), 0.0);
       y[k] = x.re;
       if (CX) y[m + k] = x.im;
     }
@@ -701,6 +701,29 @@ __device__ void warp_back_transform(const double* Rt, const double* hbeta, const
   } while (0)
 #endif
 
+// Row kernels of the dense reductions, one warp per row, lanes over columns.  The restrict
+// qualifiers tell the compiler that the row and the vector do not overlap, so it can issue the
+// loads of several columns before the stores of earlier ones: the rows live in L2 and a loop
+// that waits for each store runs at L2 latency.
+// a[j] -= s * x[j], j = j0 + lane, j0 + lane + 32, ... < j1
+__device__ __forceinline__ void row_axpy(double* __restrict__ a, const double* __restrict__ x,
+                                         double s, int j0, int j1, int lane) {
+#pragma unroll 4
+  for (int j = j0 + lane; j < j1; j += 32) a[j] -= s * x[j];
+}
+// sum over j of a[j] * x[j] (this lane's part)
+__device__ __forceinline__ double row_dot(const double* __restrict__ a, const double* __restrict__ x,
+                                          int j0, int j1, int lane) {
+  double s0 = 0.0, s1 = 0.0;
+  int j = j0 + lane;
+  for (; j + 32 < j1; j += 64) {
+    s0 = fma(a[j], x[j], s0);
+    s1 = fma(a[j + 32], x[j + 32], s1);
+  }
+  if (j < j1) s0 = fma(a[j], x[j], s0);
+  return s0 + s1;
+}
+
 // Dense solver for one problem, run by the whole CTA (dsm: up to 200 KB of shared memory).
 __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
   const int m = pb.m;
@@ -742,13 +765,18 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
     if (t == 0) *pb.status = sh.iscal[1];
     return;
   }
-  for (int64_t idx = t; idx < mm; idx += nt) {
-    const int i = (int)(idx / m), j = (int)(idx % m);
-    const double sv = pb.S[idx] * dsc[i] * dsc[j];
-    const double hv = pb.H[idx] * dsc[i] * dsc[j];
-    if (!isfinite(sv) || !isfinite(hv)) sh.iscal[1] = ST_NONFINITE;
-    L[idx] = sv;
-    A[idx] = hv;
+  // (rows over warps, columns over lanes: coalesced, no index division)
+  const int rw = t >> 5, rl = t & 31, rnw = nt >> 5;
+  for (int i = rw; i < m; i += rnw) {
+    const double di = dsc[i];
+    for (int j = rl; j < m; j += 32) {
+      const int64_t idx = (int64_t)i * m + j;
+      const double sv = pb.S[idx] * di * dsc[j];
+      const double hv = pb.H[idx] * di * dsc[j];
+      if (!isfinite(sv) || !isfinite(hv)) sh.iscal[1] = ST_NONFINITE;
+      L[idx] = sv;
+      A[idx] = hv;
+    }
   }
   __syncthreads();
   if (sh.iscal[1] != ST_OK) {
@@ -776,14 +804,7 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
       col[i] = v;
     }
     __syncthreads();
-    const int r = m - k - 1;
-    for (int64_t idx = t; idx < (int64_t)r * r; idx += nt) {
-      const int ii = (int)(idx / r), jj = (int)(idx % r);
-      if (jj <= ii) {
-        const int i = k + 1 + ii, j = k + 1 + jj;
-        L[(int64_t)i * m + j] -= col[i] * col[j];
-      }
-    }
+    for (int i = k + 1 + rw; i < m; i += rnw) row_axpy(L + (int64_t)i * m, col, col[i], k + 1, i + 1, rl);
     __syncthreads();
   }
   if (sh.iscal[1] != ST_OK) {
@@ -799,11 +820,8 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
       col[j] = v;
     }
     __syncthreads();
-    const int r = m - k - 1;
-    for (int64_t idx = t; idx < (int64_t)r * m; idx += nt) {
-      const int i = k + 1 + (int)(idx / m), j = (int)(idx % m);
-      A[(int64_t)i * m + j] -= L[(int64_t)i * m + k] * col[j];
-    }
+    for (int i = k + 1 + rw; i < m; i += rnw)
+      row_axpy(A + (int64_t)i * m, col, L[(int64_t)i * m + k], 0, m, rl);
     __syncthreads();
   }
   // ---- 2c. A <- A L^-T (column forward substitution) ----
@@ -813,13 +831,10 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
       const double v = A[(int64_t)i * m + k] * inv;
       A[(int64_t)i * m + k] = v;
       col[i] = v;
+      vtmp[i] = L[(int64_t)i * m + k];            // column k of L, read once
     }
     __syncthreads();
-    const int r = m - k - 1;
-    for (int64_t idx = t; idx < (int64_t)m * r; idx += nt) {
-      const int i = (int)(idx / r), j = k + 1 + (int)(idx % r);
-      A[(int64_t)i * m + j] -= L[(int64_t)j * m + k] * col[i];
-    }
+    for (int i = rw; i < m; i += rnw) row_axpy(A + (int64_t)i * m, vtmp, col[i], k + 1, m, rl);
     __syncthreads();
   }
   EIG_MARK(2);
@@ -847,25 +862,44 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
     const double beta = sh.scal[1], v0 = sh.scal[2];
     if (t == 0) hbeta[k] = beta;
     // u = (1, x[1:]/v0) into col[k+1..m-1]
-    for (int i = k + 1 + t; i < m; i += nt) col[i] = (i == k + 1) ? 1.0 : A[(int64_t)i * m + k] / v0;
+    const double rv0 = rcp_nr(v0);
+    for (int i = k + 1 + t; i < m; i += nt) col[i] = (i == k + 1) ? 1.0 : A[(int64_t)i * m + k] * rv0;
     __syncthreads();
     if (beta != 0.0) {
-      // left: rows k+1.., columns k.. (column-owned)
-      for (int j = k + t; j < m; j += nt) {
-        double wj = 0.0;
-        for (int i = k + 1; i < m; ++i) wj += col[i] * A[(int64_t)i * m + j];
-        wj *= beta;
-        for (int i = k + 1; i < m; ++i) A[(int64_t)i * m + j] -= wj * col[i];
+      // left: rows k+1.., columns k..: w = beta u^T A from per-warp partial sums over rows
+      // (each warp a slice of the rows, lanes over columns: coalesced, loads independent),
+      // then A -= u w
+      double* wpart = dsm;                          // rnw x m (shared memory is free here)
+      for (int jc = k; jc < m; jc += 32) {
+        const int j = jc + rl;
+        if (j < m) {
+          const double* __restrict__ aj = A + j;
+          const double* __restrict__ u = col;
+          double acc0 = 0.0, acc1 = 0.0;
+          int i = k + 1 + rw;
+          for (; i + rnw < m; i += 2 * rnw) {
+            acc0 = fma(u[i], aj[(int64_t)i * m], acc0);
+            acc1 = fma(u[i + rnw], aj[(int64_t)(i + rnw) * m], acc1);
+          }
+          if (i < m) acc0 = fma(u[i], aj[(int64_t)i * m], acc0);
+          wpart[rw * m + j] = acc0 + acc1;
+        }
       }
+      __syncthreads();
+      for (int j = k + t; j < m; j += nt) {
+        double sum = 0.0;
+        for (int w2 = 0; w2 < rnw; ++w2) sum += wpart[w2 * m + j];
+        vtmp[j] = beta * sum;
+      }
+      __syncthreads();
+      for (int i = k + 1 + rw; i < m; i += rnw) row_axpy(A + (int64_t)i * m, vtmp, col[i], k, m, rl);
       __syncthreads();
       // right: all rows, columns k+1.. (warp per row)
       const int lane = t & 31, wid = t >> 5, nw = nt >> 5;
       for (int i = wid; i < m; i += nw) {
-        double zi = 0.0;
-        for (int j = k + 1 + lane; j < m; j += 32) zi += A[(int64_t)i * m + j] * col[j];
+        double zi = row_dot(A + (int64_t)i * m, col, k + 1, m, lane);
         for (int o = 16; o > 0; o >>= 1) zi += __shfl_xor_sync(0xffffffffu, zi, o);
-        zi *= beta;
-        for (int j = k + 1 + lane; j < m; j += 32) A[(int64_t)i * m + j] -= zi * col[j];
+        row_axpy(A + (int64_t)i * m, col, zi * beta, k + 1, m, lane);
       }
       __syncthreads();
     }
@@ -875,12 +909,13 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
   }
   // ---- Hessenberg copies: Hh (inverse iteration) and the QR working copy in W ----
   double amx = 0.0;
-  for (int64_t idx = t; idx < mm; idx += nt) {
-    const int i = (int)(idx / m), j = (int)(idx % m);
-    const double v = (j >= i - 1) ? A[idx] : 0.0;
-    Hh[idx] = v;
-    amx = fmax(amx, fabs(v));
-  }
+  for (int i = rw; i < m; i += rnw)
+    for (int j = rl; j < m; j += 32) {
+      const int64_t idx = (int64_t)i * m + j;
+      const double v = (j >= i - 1) ? A[idx] : 0.0;
+      Hh[idx] = v;
+      amx = fmax(amx, fabs(v));
+    }
   const double anorm = fmax(block_max(amx, sh.red), 1e-300);
   // the QR runs on the matrix scaled by a power of two to max |entry| in [1/2, 1)
   int gex;
@@ -1091,10 +1126,9 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
     }
   }
   // Householder vectors as rows for coalesced per-warp back-transformation (W is free now)
-  for (int64_t idx = t; idx < mm; idx += nt) {
-    const int k = (int)(idx / m), i = (int)(idx % m);
-    W[idx] = (i >= k + 2 && k < m - 2) ? A[(int64_t)i * m + k] : 0.0;
-  }
+  for (int k = rw; k < m; k += rnw)
+    for (int i = rl; i < m; i += 32)
+      W[(int64_t)k * m + i] = (i >= k + 2 && k < m - 2) ? A[(int64_t)i * m + k] : 0.0;
   __syncthreads();
   if (sh.iscal[4] != 0) {
     if (t == 0) *pb.status = ST_NOCONV;
@@ -1197,12 +1231,90 @@ __device__ double dotv(const double* a, const double* b, int m, Shared& sh) {
   return block_sum(p, sh.red);
 }
 
+// Control block of the grid-wide Davidson (global memory, zeroed before the launch).
+struct DavCtl {
+  unsigned int count;      // grid barrier: arrivals in the current generation
+  unsigned int gen;        // grid barrier: generation
+  int cmd;                 // 1: matrix-vector products of x, 0: done
+  int err;                 // a barrier wait ran out
+  const double* x;
+};
+constexpr uint32_t kGridSpinLimit = 1u << 24;
+
+// Grid barrier of a cooperative launch (all CTAs resident), bounded: a wait that runs out sets
+// err and returns false on every CTA that gives up.
+__device__ bool grid_barrier(DavCtl* c, int* ok_smem) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = &c->gen;
+    const unsigned int g = *vgen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&c->count, 1u) == gridDim.x - 1) {
+      atomicExch(&c->count, 0u);
+      __threadfence();
+      atomicAdd(&c->gen, 1u);
+    } else {
+      uint32_t i = 0;
+      while (*vgen == g) {
+        if (++i > kGridSpinLimit || *(volatile int*)&c->err) {
+          ok = 0;
+          atomicExch(&c->err, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    *ok_smem = ok;
+  }
+  __syncthreads();
+  return *ok_smem != 0;
+}
+
+// This CTA's rows of y_H = H x and y_S = S x: global warp w takes rows w, w + all warps, ...;
+// x is read past L1 (CTA 0 rewrites it between products).
+__device__ void grid_rows_matvec(const double* __restrict__ H, const double* __restrict__ S, int m,
+                                 const double* x, double* yH, double* yS) {
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int i = gw; i < m; i += nw) {
+    const double* __restrict__ hr = H + (int64_t)i * m;
+    const double* __restrict__ sr = S + (int64_t)i * m;
+    double h0 = 0.0, h1 = 0.0, s0 = 0.0, s1 = 0.0;
+    int j = lane;
+    for (; j + 32 < m; j += 64) {
+      const double xa = __ldcg(x + j), xb = __ldcg(x + j + 32);
+      h0 = fma(hr[j], xa, h0);
+      s0 = fma(sr[j], xa, s0);
+      h1 = fma(hr[j + 32], xb, h1);
+      s1 = fma(sr[j + 32], xb, s1);
+    }
+    if (j < m) {
+      const double xa = __ldcg(x + j);
+      h0 = fma(hr[j], xa, h0);
+      s0 = fma(sr[j], xa, s0);
+    }
+    double h = h0 + h1, sv = s0 + s1;
+    for (int o = 16; o > 0; o >>= 1) {
+      h += __shfl_xor_sync(0xffffffffu, h, o);
+      sv += __shfl_xor_sync(0xffffffffu, sv, o);
+    }
+    if (lane == 0) {
+      yH[i] = h;
+      yS[i] = sv;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kEigThreads)
-davidson_kernel(const EigProblem* __restrict__ probs, double tol, int max_iter) {
+davidson_kernel(const EigProblem* __restrict__ probs, double tol, int max_iter, DavCtl* ctl) {
   extern __shared__ double dsm[];
   __shared__ Shared sh;
   __shared__ double hk[kDavMax * kDavMax];
-  const EigProblem pb = probs[blockIdx.x];
+  __shared__ int bar_ok;
+  const EigProblem pb = probs[0];
   const int m = pb.m;
   const int t = threadIdx.x, nt = blockDim.x;
   double* V = pb.work;                       // kDavMax x m
@@ -1222,6 +1334,42 @@ davidson_kernel(const EigProblem* __restrict__ probs, double tol, int max_iter) 
   double* sLam = sW + eig_total_doubles(ks);
   double* sVec = sLam + 2;
   int32_t* sStat = reinterpret_cast<int32_t*>(sVec + ks);
+  double* yHs = sVec + ks + 2;               // matvec results of all CTAs (m each)
+  double* ySs = yHs + m;
+
+  // CTAs other than 0 only compute their rows of the matrix-vector products CTA 0 asks for
+  if (blockIdx.x != 0) {
+    for (;;) {
+      if (!grid_barrier(ctl, &bar_ok)) return;                 // command posted
+      if (((volatile DavCtl*)ctl)->cmd == 0) return;
+      grid_rows_matvec(pb.H, pb.S, m, ((volatile DavCtl*)ctl)->x, yHs, ySs);
+      if (!grid_barrier(ctl, &bar_ok)) return;                 // rows written
+    }
+  }
+  // y_H = H x, y_S = S x over the whole grid, then copied (bypassing L1) into place
+  auto grid_matvec = [&](const double* x, double* yH, double* yS) -> bool {
+    if (t == 0) {
+      ctl->x = x;
+      ctl->cmd = 1;
+      __threadfence();
+    }
+    if (!grid_barrier(ctl, &bar_ok)) return false;
+    grid_rows_matvec(pb.H, pb.S, m, x, yHs, ySs);
+    if (!grid_barrier(ctl, &bar_ok)) return false;
+    for (int i = t; i < m; i += nt) {
+      yH[i] = __ldcg(yHs + i);
+      yS[i] = __ldcg(ySs + i);
+    }
+    __syncthreads();
+    return true;
+  };
+  auto release = [&]() {
+    if (t == 0) {
+      ctl->cmd = 0;
+      __threadfence();
+    }
+    grid_barrier(ctl, &bar_ok);
+  };
 
   for (int i = t; i < m; i += nt) {
     dH[i] = pb.H[(int64_t)i * m + i];
@@ -1230,13 +1378,16 @@ davidson_kernel(const EigProblem* __restrict__ probs, double tol, int max_iter) 
   __syncthreads();
   if (!(dS[0] > 0.0)) {
     if (t == 0) *pb.status = ST_NOT_PD;
+    release();
     return;
   }
   // v_0 = e_0 / sqrt(S_00)
   for (int i = t; i < m; i += nt) V[i] = (i == 0) ? 1.0 / sqrt(dS[0]) : 0.0;
   __syncthreads();
-  matvec(pb.H, m, V, HV);
-  matvec(pb.S, m, V, SV);
+  if (!grid_matvec(V, HV, SV)) {
+    if (t == 0) *pb.status = ST_NOCONV;
+    return;
+  }
   int k = 1;
   bool fresh = true;      // projected matrix must be rebuilt (start, restart)
   double theta = 0.0;
@@ -1329,8 +1480,12 @@ davidson_kernel(const EigProblem* __restrict__ probs, double tol, int max_iter) 
         __syncthreads();
       }
     double* stv = SV + (int64_t)k * m;
+    double* htv = HV + (int64_t)k * m;
     DAV_T(3);
-    matvec(pb.S, m, tv, stv);
+    if (!grid_matvec(tv, htv, stv)) {
+      if (t == 0) *pb.status = ST_NOCONV;
+      return;
+    }
     const double nn = dotv(tv, stv, m, sh);
     if (!(nn > 1e-300)) {
       status = ST_NOCONV;
@@ -1340,9 +1495,9 @@ davidson_kernel(const EigProblem* __restrict__ probs, double tol, int max_iter) 
     for (int i = t; i < m; i += nt) {
       tv[i] *= inv;
       stv[i] *= inv;
+      htv[i] *= inv;
     }
     __syncthreads();
-    matvec(pb.H, m, tv, HV + (int64_t)k * m);
     DAV_T(4);
     ++k;
   }
@@ -1357,6 +1512,7 @@ davidson_kernel(const EigProblem* __restrict__ probs, double tol, int max_iter) 
     pb.lam[0] = theta;
   }
   for (int i = t; i < m; i += nt) pb.vec[i] = u[i];
+  release();
 }
 
 }  // namespace
@@ -1365,15 +1521,33 @@ size_t eig_work_doubles(int64_t m) { return (size_t)eig_total_doubles(m); }
 
 size_t davidson_work_doubles(int64_t m) {
   const int64_t ks = kDavMax;
-  return (size_t)(3 * ks * m + 6 * m + 2 * ks * ks + eig_total_doubles(ks) + 2 + ks + 8);
+  return (size_t)(3 * ks * m + 6 * m + 2 * ks * ks + eig_total_doubles(ks) + 2 + ks + 8 + 2 * m +
+                  sizeof(DavCtl) / 8 + 8);
 }
 
 void launch_davidson(const EigProblem* probs, int nprob, double tol, int max_iter,
                      cudaStream_t st) {
-  if (nprob <= 0) return;
+  (void)nprob;   // one problem (the combined one), spread over every SM
+  static int grid = 0;
   const int smem = 200 * 1024;
-  cudaFuncSetAttribute(davidson_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  davidson_kernel<<<nprob, kEigThreads, smem, st>>>(probs, tol, max_iter);
+  if (grid == 0) {
+    cudaFuncSetAttribute(davidson_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, davidson_kernel, kEigThreads, smem);
+    grid = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  // the control block sits at the end of the problem's workspace
+  EigProblem pb;
+  cudaMemcpyAsync(&pb, probs, sizeof(pb), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  DavCtl* ctl = reinterpret_cast<DavCtl*>(pb.work + davidson_work_doubles(pb.m) -
+                                          sizeof(DavCtl) / 8 - 4);
+  cudaMemsetAsync(ctl, 0, sizeof(DavCtl), st);
+  void* args[] = {(void*)&probs, (void*)&tol, (void*)&max_iter, (void*)&ctl};
+  cudaLaunchCooperativeKernel((const void*)davidson_kernel, dim3(grid), dim3(kEigThreads), args,
+                              smem, st);
 }
 
 void launch_eig(const EigProblem* probs, int nprob, int threads, cudaStream_t st) {
