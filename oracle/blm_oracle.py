@@ -20,7 +20,7 @@ Notation: O[s, x] = <n_s|Psi^x>/<n_s|Psi> (raw log-derivative ratios), E[s] = lo
 G[s, x] = dE_L/dmu_x, so the Hamiltonian ratio of Eq. 3 is h_x = <n|H|Psi^x>/<n|Psi> = E O_x + G_x
 (H acting on dPsi/dmu gives d(E_L Psi)/dmu).  w[s] = |Psi|^2/P (1 when P = |Psi|^2).
 
-Readings where the paper is silent (each is listed in the design doc):
+Readings where the paper is silent:
   * centring: the tangent vectors are taken as Psi^x - <O_x> Psi, a change of basis inside
     span{Psi, Psi^x}; eigenvalues and the tangent parts of eigenvectors are unchanged, and the
     update converts back with alpha = c_0 - sum_x c_x <O_x>.
