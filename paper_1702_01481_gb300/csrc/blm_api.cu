@@ -119,6 +119,7 @@ struct blm_handle {
   TcTile* d_tc1 = nullptr;  int ntc1 = 0;   // pass-1 tensor-core tiles
   TcTile* d_tc2 = nullptr;  int ntc2 = 0;   // combined tensor-core tiles
   int tc1_aligned = 0, tc2_aligned = 0;     // tile parameter offsets all multiples of 4
+  int off_aligned = 0;                     // block offsets all multiples of 4
   // host staging
   void* d_stage[2][4] = {{nullptr}};
   int64_t stage_rows = 0;
@@ -243,6 +244,9 @@ void derive(blm_handle* h, const blm_problem* p) {
   h->n = p->n_params;
   h->nb = p->n_blocks;
   h->off.assign(p->block_offsets, p->block_offsets + p->n_blocks + 1);
+  h->off_aligned = 1;
+  for (int64_t o : h->off)
+    if (o % 4 != 0) h->off_aligned = 0;
   h->K = p->n_keep;
   h->n_old = p->n_old;
   h->prec = p->precision;
@@ -541,8 +545,10 @@ blm_status project_dev(blm_handle* h, const T* O, const T* G, const T* E, const 
       const bool prepared = h->d_opA && dc <= h->n;
       {
         Prof pr(h, PC_PROJECT, prepared ? 1 : 2);
-        launch_project<float, float>(Os, Gs, ld, ld, h->d_shift, h->d_shift32, h->d_pbB, h->nb, h->d_cen, PY,
-                                     PZ, dc, cnt, h->maxM, h->maxK, st);
+        if (!launch_project_rb(Os, Gs, ld, h->d_shift ? h->d_shift32 : nullptr, h->d_pbB, h->nb,
+                               h->off_aligned != 0, h->d_cen, PY, PZ, dc, cnt, h->maxK, st))
+          launch_project<float, float>(Os, Gs, ld, ld, h->d_shift, h->d_shift32, h->d_pbB, h->nb,
+                                       h->d_cen, PY, PZ, dc, cnt, h->maxM, h->maxK, st);
         if (!prepared)
           launch_sums<float>(PY, PZ, Es, ws, cnt, dc, dc, dc, nullptr, h->d_cvec, h->d_cvec + dc,
                              h->d_cvec + 2 * dc, nullptr, true, st);

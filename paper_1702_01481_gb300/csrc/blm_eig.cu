@@ -224,12 +224,158 @@ __device__ void house3(double x, double y, double z, double& beta, double& v1, d
 struct Shared {
   double red[32];
   double scal[8];
+  double shf[8];            // multi-bulge sweep: (sum, product) of each bulge's shift pair
+  float hs[64];             // trailing block for the shifts (8 x 8, FP32)
+  float hw[16];             // its eigenvalues (re 8 | im 8)
   int iscal[8];
   int sel_idx[kMaxKeep];
   int sel_part[kMaxKeep];   // 0 real, 1 real part of complex, 2 imaginary part of complex
   int job_q0[kMaxKeep];     // eigenvector jobs: selection entries [job_q0, job_q0 + job_len)
   int job_len[kMaxKeep];
 };
+
+// ---------------------------------------------------------------------------------------------
+// Shifts of a multi-bulge sweep.  The 2 nb shifts are the eigenvalues of the trailing 2 nb x 2 nb
+// block of the active window (the usual multishift choice), computed by one thread in FP32 with
+// the plain Francis double-shift iteration: a shift only steers convergence, the sweep's
+// accuracy does not depend on it.  They are paired from the bottom of the block upwards
+// (complex conjugates together, real ones two by two) and each pair becomes one bulge's
+// (sum, product).
+// ---------------------------------------------------------------------------------------------
+constexpr int kNbMax = 4;       // bulges chased together
+
+__device__ void house3f(float x, float y, float z, float& beta, float& v1, float& v2,
+                        float& alpha) {
+  const float sigma = fmaf(z, z, y * y);
+  if (sigma == 0.0f) {
+    beta = 0.0f;
+    v1 = v2 = 0.0f;
+    alpha = x;
+    return;
+  }
+  const float mu = sqrtf(fmaf(x, x, sigma));
+  const float sg = x < 0.0f ? -1.0f : 1.0f;
+  const float v0 = fmaf(sg, mu, x);
+  v1 = y / v0;
+  v2 = z / v0;
+  beta = 1.0f + fabsf(x) / mu;
+  alpha = -sg * mu;
+}
+
+// Eigenvalues of the n x n (n <= 8) Hessenberg matrix h (row-major, leading dimension 8), in
+// place; false if the iteration does not converge.
+__device__ bool small_eigs_f32(float* h, int n, float* wr, float* wi) {
+  auto H = [&](int i, int j) -> float& { return h[i * 8 + j]; };
+  int hi = n - 1, its = 0, total = 0;
+  while (hi >= 0) {
+    int l = hi;
+    for (; l > 0; --l) {
+      float s = fabsf(H(l - 1, l - 1)) + fabsf(H(l, l));
+      if (s == 0.0f) s = 1.0f;
+      if (fabsf(H(l, l - 1)) <= 1e-6f * s) break;   // shifts need no more
+    }
+    if (l == hi) {
+      wr[hi] = H(hi, hi);
+      wi[hi] = 0.0f;
+      hi -= 1;
+      its = 0;
+      continue;
+    }
+    if (l == hi - 1) {
+      const float a = H(hi - 1, hi - 1), b = H(hi - 1, hi), c = H(hi, hi - 1), d = H(hi, hi);
+      const float p = 0.5f * (a - d), disc = p * p + b * c, mid = 0.5f * (a + d);
+      if (disc >= 0.0f) {
+        const float sq = sqrtf(disc);
+        wr[hi - 1] = mid - sq;
+        wr[hi] = mid + sq;
+        wi[hi - 1] = wi[hi] = 0.0f;
+      } else {
+        const float sq = sqrtf(-disc);
+        wr[hi - 1] = wr[hi] = mid;
+        wi[hi - 1] = sq;
+        wi[hi] = -sq;
+      }
+      hi -= 2;
+      its = 0;
+      continue;
+    }
+    if (++total > 30 * n) return false;
+    ++its;
+    float s, tt;
+    if (its % 11 == 10) {
+      const float e = fabsf(H(hi, hi - 1)) + fabsf(H(hi - 1, hi - 2));
+      s = 1.5f * e;
+      tt = e * e;
+    } else {
+      s = H(hi - 1, hi - 1) + H(hi, hi);
+      tt = H(hi - 1, hi - 1) * H(hi, hi) - H(hi - 1, hi) * H(hi, hi - 1);
+    }
+    float x = H(l, l) * H(l, l) + H(l, l + 1) * H(l + 1, l) - s * H(l, l) + tt;
+    float y = H(l + 1, l) * (H(l, l) + H(l + 1, l + 1) - s);
+    float z = H(l + 1, l) * H(l + 2, l + 1);
+    for (int k = l; k <= hi - 1; ++k) {
+      const bool three = k <= hi - 2;
+      if (k > l) {
+        x = H(k, k - 1);
+        y = H(k + 1, k - 1);
+        z = three ? H(k + 2, k - 1) : 0.0f;
+      }
+      float beta, v1, v2, alpha;
+      house3f(x, y, three ? z : 0.0f, beta, v1, v2, alpha);
+      if (!three) v2 = 0.0f;
+      if (beta == 0.0f) continue;
+      if (k > l) {
+        H(k, k - 1) = alpha;
+        H(k + 1, k - 1) = 0.0f;
+        if (three) H(k + 2, k - 1) = 0.0f;
+      }
+      for (int j = k; j <= hi; ++j) {
+        const float p = H(k, j) + v1 * H(k + 1, j) + (three ? v2 * H(k + 2, j) : 0.0f);
+        H(k, j) -= beta * p;
+        H(k + 1, j) -= beta * v1 * p;
+        if (three) H(k + 2, j) -= beta * v2 * p;
+      }
+      const int rmax = three ? min(k + 3, hi) : hi;
+      for (int i = l; i <= rmax; ++i) {
+        const float p = H(i, k) + v1 * H(i, k + 1) + (three ? v2 * H(i, k + 2) : 0.0f);
+        H(i, k) -= beta * p;
+        H(i, k + 1) -= beta * v1 * p;
+        if (three) H(i, k + 2) -= beta * v2 * p;
+      }
+    }
+  }
+  return true;
+}
+
+// (sum, product) pairs for nb bulges from the n = 2 nb eigenvalues, bottom of the block first.
+__device__ void pair_shifts(const float* wr, const float* wi, int n, int nb, double* shf) {
+  int np = 0;
+  bool have = false;
+  double pend = 0.0;
+  for (int i = n - 1; i >= 0 && np < nb;) {
+    if (wi[i] != 0.0f && i > 0) {
+      shf[2 * np] = 2.0 * (double)wr[i];
+      shf[2 * np + 1] = (double)wr[i] * wr[i] + (double)wi[i] * wi[i];
+      ++np;
+      i -= 2;
+    } else {
+      if (have) {
+        shf[2 * np] = pend + (double)wr[i];
+        shf[2 * np + 1] = pend * (double)wr[i];
+        ++np;
+        have = false;
+      } else {
+        pend = wr[i];
+        have = true;
+      }
+      i -= 1;
+    }
+  }
+  for (int j = np; j < nb; ++j) {
+    shf[2 * j] = np > 0 ? shf[0] : 0.0;
+    shf[2 * j + 1] = np > 0 ? shf[1] : 0.0;
+  }
+}
 
 // ---------------------------------------------------------------------------------------------
 // Francis double-shift QR for all eigenvalues of the Hessenberg matrix G (dense, row-major
@@ -258,8 +404,9 @@ __device__ __forceinline__ void chase_sync() {
   }
 }
 
-// shared memory the QR needs: the window and the reflectors of one window
-constexpr int kQrSmemDoubles = kWin * kWinLd + 3 * kWin;
+// shared memory the QR needs: the window and the reflectors of one window (all bulges)
+constexpr int kQrSmemDoubles = kWin * kWinLd + 4 * kWin * kNbMax;
+static_assert(kChase == 32 * kNbMax, "one chase warp per bulge slot");
 
 // Arithmetic of the QR sweep: FP64, or double words (default; FP64 when it fails).
 template <typename R>
@@ -275,6 +422,205 @@ struct QrArith<dw> {
   __device__ static dw of(double d) { return dw_of_double(d); }
 };
 
+// One QR sweep on the active window [l, hi] with nb (2..kNbMax) bulges chased together, their
+// shift pairs in sh.shf.  Bulge j starts three steps after bulge j - 1 and, at time step tau,
+// takes step k_j = l + tau - 3 j (active for l <= k_j <= hi - 1); bulges three rows apart touch
+// disjoint rows in their row operations and disjoint columns in their column operations, so one
+// time step applies all of them between two barriers:
+//   phase 1 (thread t owns column a + t): every thread forms every active bulge's reflector from
+//     its bulge column (or, at k_j = l, from the shift polynomial's first column) and applies
+//     the row operations to its column;
+//   phase 2 (thread t owns row a + t): leading bulge first, set the bulge column to (alpha, 0, 0)
+//     and apply the column operations -- a row where a trailing bulge's column operation meets
+//     the leading bulge's annihilated column receives the annihilation first, as in the
+//     unpipelined order.
+// Rows above and columns right of the window receive the same operations afterwards from the
+// stored reflectors, all bulges of one time step on a sliding run of 3 kNbMax entries (their
+// ranges are disjoint and adjacent), time steps in order.
+template <typename R>
+__device__ void multi_sweep(R* G, int m, int l, int hi, int nb, R* win, R* refl, Shared& sh) {
+  using Q = QrArith<R>;
+  const int t = threadIdx.x, nt = blockDim.x;
+  const R zero = Q::of(0.0);
+  auto g = [&](int i, int j) -> R& { return G[(int64_t)i * m + j]; };
+  const int T = (hi - 1 - l) + 1 + 3 * (nb - 1);   // time steps of the sweep
+  const int kSteps = kWin - 3 * kNbMax - 1;        // time steps per window
+  for (int ts = 0; ts < T;) {
+    const int te = min(ts + kSteps - 1, T - 1);
+    const int a = max(l, l + ts - 3 * (nb - 1) - 1);   // window rows / columns a..b
+    const int b = min(hi, l + te + 3);
+    const int w = b - a + 1;
+    for (int idx = t; idx < w * w; idx += nt) {
+      const int r = idx / w, c = idx - r * w;
+      win[r * kWinLd + c] = g(a + r, a + c);
+    }
+    __syncthreads();
+    if (t < kChase) {
+      auto W = [&](int i, int j) -> R& { return win[(i - a) * kWinLd + (j - a)]; };
+      auto clampw = [&](int i) { return min(max(i, a), b); };
+      for (int tau = ts; tau <= te; ++tau) {
+        R* rft = refl + (tau - ts) * kNbMax * 4;   // (beta, v1, v2, alpha) of each slot
+        {
+          // phase 0: warp j forms slot j's reflector from its bulge column (or, at k = l, from
+          // the shift polynomial's first column)
+          const int j = t >> 5;
+          const int k = l + tau - 3 * j;
+          R be = zero, w1 = zero, w2 = zero, al = zero;
+          if (j < nb && k >= l && k <= hi - 1) {
+            const bool three = k <= hi - 2;
+            R x, y, z;
+            if (k == l) {
+              const R s = Q::of(sh.shf[2 * j]), tt = Q::of(sh.shf[2 * j + 1]);
+              const R h00 = W(l, l), h10 = W(l + 1, l), h01 = W(l, l + 1);
+              const R h11 = W(l + 1, l + 1), h21 = W(l + 2, l + 1);
+              x = h00 * h00 + h01 * h10 - s * h00 + tt;
+              y = h10 * (h00 + h11 - s);
+              z = h10 * h21;
+            } else {
+              x = W(k, k - 1);
+              y = W(k + 1, k - 1);
+              z = three ? W(k + 2, k - 1) : zero;
+            }
+            house3(x, y, three ? z : zero, be, w1, w2, al);
+            if (!three) w2 = zero;
+          }
+          if ((t & 31) == 0) {
+            rft[4 * j] = be;
+            rft[4 * j + 1] = w1;
+            rft[4 * j + 2] = w2;
+            rft[4 * j + 3] = al;
+          }
+        }
+        chase_sync();
+        // phases 1 and 2: every slot's work from clamped (valid) indices, kept or dropped by
+        // predicated stores, so that the slots' dependent chains overlap
+        R be[kNbMax], v1[kNbMax], v2[kNbMax], al[kNbMax], bv1[kNbMax], bv2[kNbMax];
+        bool act[kNbMax];
+#pragma unroll
+        for (int j = 0; j < kNbMax; ++j) {
+          const int k = l + tau - 3 * j;
+          be[j] = rft[4 * j];
+          v1[j] = rft[4 * j + 1];
+          v2[j] = rft[4 * j + 2];
+          al[j] = rft[4 * j + 3];
+          act[j] = j < nb && k >= l && k <= hi - 1;
+          bv1[j] = be[j] * v1[j];
+          bv2[j] = be[j] * v2[j];
+        }
+        const int c = a + t;   // phase 1: row operations on column c (slots touch disjoint rows)
+        if (c <= b) {
+          R n[kNbMax][3];
+#pragma unroll
+          for (int j = 0; j < kNbMax; ++j) {
+            const int k = l + tau - 3 * j;
+            const R r0 = W(clampw(k), c), r1 = W(clampw(k + 1), c), r2 = W(clampw(k + 2), c);
+            const R p = r0 + (v1[j] * r1 + v2[j] * r2);
+            n[j][0] = r0 - be[j] * p;
+            n[j][1] = r1 - bv1[j] * p;
+            n[j][2] = r2 - bv2[j] * p;
+          }
+#pragma unroll
+          for (int j = 0; j < kNbMax; ++j) {
+            const int k = l + tau - 3 * j;
+            if (act[j] && mag(be[j]) != 0 && c >= k) {
+              W(k, c) = n[j][0];
+              W(k + 1, c) = n[j][1];
+              if (k <= hi - 2) W(k + 2, c) = n[j][2];
+            }
+          }
+        }
+        chase_sync();
+        const int r = a + t;   // phase 2: bulge columns and column operations on row r
+        if (r <= b) {
+          R n[kNbMax][3];
+#pragma unroll
+          for (int j = 0; j < kNbMax; ++j) {
+            const int k = l + tau - 3 * j;
+            const R c0 = W(r, clampw(k)), c1 = W(r, clampw(k + 1));
+            R c2 = W(r, clampw(k + 2));
+            if (j > 0) {
+              // column k + 2 is the leading slot's bulge column; on its row k + 3 that slot
+              // writes alpha first (below), which this slot's operation must see
+              const int kl = k + 3;
+              if (act[j - 1] && mag(be[j - 1]) != 0 && kl > l && r == kl) c2 = al[j - 1];
+            }
+            const R p = c0 + (v1[j] * c1 + v2[j] * c2);
+            n[j][0] = c0 - be[j] * p;
+            n[j][1] = c1 - bv1[j] * p;
+            n[j][2] = c2 - bv2[j] * p;
+          }
+#pragma unroll
+          for (int j = 0; j < kNbMax; ++j) {
+            const int k = l + tau - 3 * j;
+            if (act[j] && mag(be[j]) != 0) {
+              const bool three = k <= hi - 2;
+              if (k > l && r >= k && r <= k + (three ? 2 : 1)) W(r, k - 1) = (r == k) ? al[j] : zero;
+              const int rmax = three ? min(k + 3, hi) : hi;
+              if (r <= rmax) {
+                W(r, k) = n[j][0];
+                W(r, k + 1) = n[j][1];
+                if (three) W(r, k + 2) = n[j][2];
+              }
+            }
+          }
+        }
+        chase_sync();
+      }
+    }
+    __syncthreads();
+    for (int idx = t; idx < w * w; idx += nt) {
+      const int r = idx / w, c = idx - r * w;
+      g(a + r, a + c) = win[r * kWinLd + c];
+    }
+    // rows l..a-1 (column operations, walking right) and columns b+1..hi (row operations,
+    // walking down); entry i of the run is position p0 + i, bulge j on entries 9-3j..11-3j
+    const int nfa = a - l, nfb = hi - b;
+    for (int u = t; u < nfa + nfb; u += nt) {
+      const bool row_walk = u < nfa;
+      const int64_t base = row_walk ? (int64_t)(l + u) * m : (int64_t)(b + 1 + u - nfa);
+      const int64_t step = row_walk ? 1 : m;
+      auto ld = [&](int e) { return (e >= a && e <= b) ? G[base + (int64_t)e * step] : zero; };
+      auto st = [&](int e, const R& v) {
+        if (e >= a && e <= b) G[base + (int64_t)e * step] = v;
+      };
+      int p0 = l + ts - 3 * (kNbMax - 1);
+      R e[3 * kNbMax], q[4];
+#pragma unroll
+      for (int i = 0; i < 3 * kNbMax; ++i) e[i] = ld(p0 + i);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) q[i] = ld(p0 + 3 * kNbMax + i);
+      for (int tau = ts; tau <= te; ++tau) {
+        const R* rf = refl + (tau - ts) * kNbMax * 4;
+#pragma unroll
+        for (int j = 0; j < kNbMax; ++j) {
+          // inactive slots carry beta = 0 and leave their entries unchanged exactly
+          const R beta = rf[4 * j], w1 = rf[4 * j + 1], w2 = rf[4 * j + 2];
+          R& x0 = e[3 * (kNbMax - 1 - j)];
+          R& x1 = e[3 * (kNbMax - 1 - j) + 1];
+          R& x2 = e[3 * (kNbMax - 1 - j) + 2];
+          const R p = x0 + (w1 * x1 + w2 * x2);
+          x0 = x0 - beta * p;
+          x1 = x1 - (beta * w1) * p;
+          x2 = x2 - (beta * w2) * p;
+        }
+        st(p0, e[0]);
+#pragma unroll
+        for (int i = 0; i < 3 * kNbMax - 1; ++i) e[i] = e[i + 1];
+        e[3 * kNbMax - 1] = q[0];
+        q[0] = q[1];
+        q[1] = q[2];
+        q[2] = q[3];
+        q[3] = ld(p0 + 3 * kNbMax + 4);
+        ++p0;
+      }
+#pragma unroll
+      for (int i = 0; i < 3 * kNbMax; ++i) st(p0 + i, e[i]);
+    }
+    __syncthreads();
+    ts = te + 1;
+  }
+}
+
 template <typename R>
 __device__ bool hqr_windowed(R* G, int m, double* wr, double* wi, double anorm, double* dsm,
                              Shared& sh) {
@@ -289,7 +635,7 @@ __device__ bool hqr_windowed(R* G, int m, double* wr, double* wi, double anorm, 
   const int limit = 40 * m + 100;
   auto g = [&](int i, int j) -> R& { return G[(int64_t)i * m + j]; };
 #ifdef BLM_EIG_TIMING
-  long long qt[4] = {0, 0, 0, 0}, qc = 0, nsweep = 0, nstep = 0;
+  long long qt[4] = {0, 0, 0, 0}, qc = 0, nsweep = 0, nstep = 0, nmulti = 0, nsfail = 0;
 #define QR_T0() (qc = clock64())
 #define QR_T(i) (qt[i] += clock64() - qc, qc = clock64())
 #else
@@ -352,6 +698,45 @@ __device__ bool hqr_windowed(R* G, int m, double* wr, double* wi, double anorm, 
     ++nsweep;
     nstep += hi - l;
 #endif
+    const int nact = hi - l + 1;
+    const int nb = (its % 11 == 10) ? 1 : (nact >= 40 ? kNbMax : (nact >= 20 ? 2 : 1));
+#ifdef BLM_EIG_TIMING
+    nstep += (long long)(nb - 1) * (hi - l);   // bulge steps
+#endif
+    if (nb > 1) {
+      // --- multi-bulge sweep: shifts from the trailing 2 nb x 2 nb block (thread 0) ---
+      if (t == 0) {
+        if (l > 0) g(l, l - 1) = zero;
+        const int n = 2 * nb, o = hi - n + 1;
+        for (int i = 0; i < n; ++i)
+          for (int j = 0; j < n; ++j)
+            sh.hs[i * 8 + j] = (j >= i - 1) ? (float)to_double(g(o + i, o + j)) : 0.0f;
+#ifdef BLM_EIG_TIMING
+        ++nmulti;
+#endif
+        if (small_eigs_f32(sh.hs, n, sh.hw, sh.hw + 8)) {
+          pair_shifts(sh.hw, sh.hw + 8, n, nb, sh.shf);
+          // the leading bulge takes the Francis shifts of the trailing 2 x 2 in full precision
+          sh.shf[0] = to_double(g(hi - 1, hi - 1) + g(hi, hi));
+          sh.shf[1] = to_double(g(hi - 1, hi - 1) * g(hi, hi) - g(hi - 1, hi) * g(hi, hi - 1));
+        } else {
+#ifdef BLM_EIG_TIMING
+          ++nsfail;
+#endif
+          // the trailing 2 x 2 diagonal blocks' eigenvalues
+          for (int j = 0; j < nb; ++j) {
+            const int i0 = hi - 2 * j - 1;
+            sh.shf[2 * j] = to_double(g(i0, i0) + g(i0 + 1, i0 + 1));
+            sh.shf[2 * j + 1] = to_double(g(i0, i0) * g(i0 + 1, i0 + 1) - g(i0, i0 + 1) * g(i0 + 1, i0));
+          }
+        }
+      }
+      __syncthreads();
+      QR_T(0);
+      multi_sweep<R>(G, m, l, hi, nb, win, refl, sh);
+      QR_T(2);
+      continue;
+    }
     // --- shifts and the first column of the double-shift polynomial (thread 0) ---
     if (t == 0) {
       if (l > 0) g(l, l - 1) = zero;
@@ -504,8 +889,9 @@ __device__ bool hqr_windowed(R* G, int m, double* wr, double* wi, double anorm, 
   }
 #ifdef BLM_EIG_TIMING
   if (t == 0 && blockIdx.x == 0)
-    printf("qr m=%d sweeps %lld steps %lld: deflate+shift %lld window-load %lld chase %lld far %lld cycles\n",
-           m, nsweep, nstep, qt[0], qt[1], qt[2], qt[3]);
+    printf("qr m=%d sweeps %lld (multi-bulge %lld, shift failures %lld) steps %lld: deflate+shift %lld "
+           "window-load %lld chase %lld far %lld cycles\n",
+           m, nsweep, nmulti, nsfail, nstep, qt[0], qt[1], qt[2], qt[3]);
 #endif
 #undef QR_T0
 #undef QR_T

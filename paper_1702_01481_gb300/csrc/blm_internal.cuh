@@ -72,6 +72,13 @@ void launch_sums(const T* Y, const T* Z, const T* E, const T* w, int64_t ns, int
                  cudaStream_t st);
 void launch_contract(const Seg* segs, const Tile* tiles, int ntiles, const SrcArgs& src,
                      int64_t ns, int splits, cudaStream_t st);
+// Register-blocked FP32 projection (mixed path).  Returns false, launching nothing, where it
+// does not apply: more than 20 directions in a block, block offsets (offsets_aligned) or the
+// row stride not multiples of 4 floats, or sample arrays not 16-byte aligned.
+bool launch_project_rb(const float* O, const float* G, int64_t ld, const float* shift32,
+                       const ProjBlock* blocks, int nblocks, bool offsets_aligned,
+                       const double* cen, float* Y, float* Z, int64_t ldout, int64_t ns,
+                       int max_nd, cudaStream_t st);
 template <typename T, typename TO>
 void launch_project(const T* O, const T* G, int64_t ldo, int64_t ldg, const double* shift,
                     const float* shift32,

@@ -405,6 +405,160 @@ project_tiled_kernel(const T* __restrict__ O, const T* __restrict__ G, int64_t l
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Register-blocked FP32 projection (mixed path; blocks of up to 20 directions whose parameter
+// offsets and sample rows are 16-byte aligned).  A CTA of four warps takes 256 samples of one
+// block: warps 0-1 form O' = O - c, warps 2-3 read G, and each lane owns four samples (rows
+// lane + 32 s of its warp's 128) times all 20 directions, so a 16-byte shared load of four
+// parameters of one sample feeds 80 products and every direction load is a broadcast.  The
+// products use paired FP32 FMAs (fma.rn.f32x2: two independent round-to-nearest FMAs, bit for
+// bit the scalar ones, so the sums equal project_tiled_kernel's).  Runs of 16 parameters are
+// staged by 16-byte cp.async, three stages in flight; sample rows are 64 bytes with their four
+// 16-byte chunks XOR-swizzled by bits 1-2 of the row, so that the eight rows of a quarter-warp
+// load, and the eight chunks of a quarter-warp's copies, fall in different bank groups.
+// ---------------------------------------------------------------------------------------------
+constexpr int kRbThreads = 128;
+constexpr int kRbS = 256;       // samples per CTA
+constexpr int kRbC = 16;        // parameters per stage
+constexpr int kRbJ = 20;        // directions per thread
+constexpr int kRbStages = 3;
+constexpr int kRbTile = kRbS * kRbC;                       // floats of one O or G stage
+constexpr int kRbStage = 2 * kRbTile + kRbC * kRbJ + kRbC;  // O, G, D [c][j], shift
+constexpr size_t kRbSmem = sizeof(float) * kRbStages * kRbStage;
+
+__device__ __forceinline__ int rb_swz(int r, int q) { return r * kRbC + ((q ^ ((r >> 1) & 3)) << 2); }
+
+__device__ __forceinline__ void ffma2(unsigned long long& acc, unsigned long long a,
+                                      unsigned long long b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+
+__device__ __forceinline__ unsigned long long dup2(float x) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(bytes)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kRbThreads, 2)
+project_rb_kernel(const float* __restrict__ O, const float* __restrict__ G, int64_t ld,
+                  const float* __restrict__ shift32, const ProjBlock* __restrict__ blocks,
+                  const double* __restrict__ cen, float* __restrict__ Y, float* __restrict__ Z,
+                  int64_t ldout, int64_t ns) {
+  extern __shared__ __align__(16) float rb_smem[];
+  const ProjBlock pb = blocks[blockIdx.y];
+  const int64_t s_base = (int64_t)blockIdx.x * kRbS;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const bool isO = warp < 2;
+  const int nruns = (pb.m + kRbC - 1) / kRbC;
+
+  auto issue = [&](int r) {
+    if (r < nruns) {
+      float* stg = rb_smem + (r % kRbStages) * kRbStage;
+      const int p0 = r * kRbC;
+      const int pc = min(kRbC, pb.m - p0);
+#pragma unroll 4
+      for (int idx = t; idx < 2 * kRbS * 4; idx += kRbThreads) {
+        const int op = idx >> 10, i = idx & 1023, row = i >> 2, q = i & 3;
+        const int64_t s = s_base + row;
+        const int rem = (pc - 4 * q) * 4;
+        const int bytes = s < ns ? (rem < 0 ? 0 : (rem > 16 ? 16 : rem)) : 0;
+        const float* base = op ? G : O;
+        const float* src = bytes ? base + s * ld + pb.lo + p0 + 4 * q : base;
+        cp_async16(stg + op * kRbTile + rb_swz(row, q), src, bytes);
+      }
+      float* ds = stg + 2 * kRbTile;
+      for (int idx = t; idx < kRbC * kRbJ; idx += kRbThreads) {
+        const int c = idx / kRbJ, j = idx - c * kRbJ;
+        const bool ok = j < pb.nd && c < pc;
+        cp_async_elem(ds + idx, pb.dir32 + (ok ? (int64_t)j * pb.dld + p0 + c : 0), ok);
+      }
+      if (t < kRbC) {
+        const bool ok = shift32 != nullptr && t < pc;
+        cp_async_elem(ds + kRbC * kRbJ + t, ok ? shift32 + pb.lo + p0 + t : pb.dir32, ok);
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+
+  unsigned long long acc[4][kRbJ / 2];
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+#pragma unroll
+    for (int j = 0; j < kRbJ / 2; ++j) acc[s][j] = 0ull;
+
+  const int rbase = (warp & 1) * 128 + lane;
+  issue(0);
+  issue(1);
+  for (int r = 0; r < nruns; ++r) {
+    issue(r + 2);
+    asm volatile("cp.async.wait_group 2;" ::: "memory");
+    __syncthreads();
+    const float* stg = rb_smem + (r % kRbStages) * kRbStage;
+    const float* tile = stg + (isO ? 0 : kRbTile);
+    const float* ds = stg + 2 * kRbTile;
+#pragma unroll
+    for (int c4 = 0; c4 < kRbC / 4; ++c4) {
+      float4 o[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+        o[s] = *reinterpret_cast<const float4*>(tile + rb_swz(rbase + 32 * s, c4));
+      if (isO) {
+        const float4 sh = *reinterpret_cast<const float4*>(ds + kRbC * kRbJ + 4 * c4);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          o[s].x -= sh.x; o[s].y -= sh.y; o[s].z -= sh.z; o[s].w -= sh.w;
+        }
+      }
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        unsigned long long od[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+          od[s] = dup2(cc == 0 ? o[s].x : cc == 1 ? o[s].y : cc == 2 ? o[s].z : o[s].w);
+        const float* drow = ds + (4 * c4 + cc) * kRbJ;
+#pragma unroll
+        for (int jq = 0; jq < kRbJ / 4; ++jq) {
+          const ulonglong2 dd = *reinterpret_cast<const ulonglong2*>(drow + 4 * jq);
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            ffma2(acc[s][2 * jq], od[s], dd.x);
+            ffma2(acc[s][2 * jq + 1], od[s], dd.y);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+
+  float* out = isO ? Y : Z;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int64_t smp = s_base + rbase + 32 * s;
+    if (smp >= ns) continue;
+#pragma unroll
+    for (int jp = 0; jp < kRbJ / 2; ++jp) {
+      float v0, v1;
+      asm("mov.b64 {%0, %1}, %2;" : "=f"(v0), "=f"(v1) : "l"(acc[s][jp]));
+      const int j0 = 2 * jp;
+      if (j0 < pb.nd) {
+        const int64_t oc = pb.oc + j0;
+        out[smp * ldout + oc] = (isO && cen) ? v0 - (float)cen[oc] : v0;
+      }
+      if (j0 + 1 < pb.nd) {
+        const int64_t oc = pb.oc + j0 + 1;
+        out[smp * ldout + oc] = (isO && cen) ? v1 - (float)cen[oc] : v1;
+      }
+    }
+  }
+}
+
 int splits_for(int64_t ns, int64_t granule, int64_t max_splits) {
   int64_t s = (ns + granule - 1) / granule;
   if (s > max_splits) s = max_splits;
@@ -450,6 +604,22 @@ void launch_contract(const Seg* segs, const Tile* tiles, int ntiles, const SrcAr
   splits = (int)((ns + per - 1) / per);
   dim3 grid((unsigned)ntiles, (unsigned)splits);
   contract_kernel<<<grid, kThreads, 0, st>>>(segs, tiles, src, ns, per);
+}
+
+bool launch_project_rb(const float* O, const float* G, int64_t ld, const float* shift32,
+                       const ProjBlock* blocks, int nblocks, bool offsets_aligned,
+                       const double* cen, float* Y, float* Z, int64_t ldout, int64_t ns,
+                       int max_nd, cudaStream_t st) {
+  if (!offsets_aligned || max_nd > kRbJ || ld % 4 != 0 ||
+      (((uintptr_t)O | (uintptr_t)G) & 15) != 0)
+    return false;
+  if (ns <= 0 || nblocks <= 0) return true;
+  cudaFuncSetAttribute(project_rb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)kRbSmem);
+  dim3 grid((unsigned)((ns + kRbS - 1) / kRbS), (unsigned)nblocks);
+  project_rb_kernel<<<grid, kRbThreads, kRbSmem, st>>>(O, G, ld, shift32, blocks, cen, Y, Z,
+                                                       ldout, ns);
+  return true;
 }
 
 template <typename T, typename TO>

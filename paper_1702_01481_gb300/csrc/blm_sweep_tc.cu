@@ -66,10 +66,13 @@ struct Bars {
   uint64_t f_empty[3];
   uint64_t l1_full;
   uint64_t l1_empty;
+  uint64_t db_full[2];       // prepared-operand kernel: double-buffered accumulator
+  uint64_t db_empty[2];
   uint64_t drain;
   uint32_t tmem_base;
   int32_t abort;
 };
+static_assert(sizeof(Bars) <= 256, "barrier block exceeds its shared-memory slot");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -185,6 +188,19 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),        \
       "r"(r[29]), "r"(r[30]), "r"(r[31])                                                          \
       : "memory")
+
+#define TMEM_LD8(taddr, r)                                                                        \
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"          \
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),          \
+                 "=r"(r[6]), "=r"(r[7])                                                           \
+               : "r"(taddr))
+
+#define TMEM_ST8(taddr, r)                                                                        \
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(   \
+                   taddr),                                                                        \
+               "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),       \
+               "r"(r[7])                                                                          \
+               : "memory")
 
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -414,12 +430,18 @@ __device__ __forceinline__ float preload_coef(int i, int nst, int fs) {
   return -0.5f * (float)interval_len(i, nst, fs) / (float)(1 + (i - 1) * fs);
 }
 
-// Epilogue role (warps 4-7, one per 32-lane tensor-memory quadrant): at the end of each
-// accumulator interval add L1 into L2 (or, at the end of a unit, L2 + L1 into the FP64 sums).
-template <int SK>
+// Epilogue role (NW = 4 warps 4-7, one per 32-lane tensor-memory quadrant, or NW = 8 warps
+// 4-11, two per quadrant each taking 128 of the 256 columns): at the end of each accumulator
+// interval add L1 into L2 (or, at the end of a unit, L2 + L1 into the FP64 sums) and preload L1.
+// The MMA warp waits for this drain before the next interval, so it is kept short: with eight
+// warps columns move in pairs of 32-column chunks (four tensor-memory loads per wait).
+template <int SK, int NW>
 __device__ __forceinline__ void epilogue_role(const Params& P, Bars* bars, uint32_t tmem, int warp,
                                               int lane, int fs) {
-  const int q = warp & 3;                         // tensor-memory lane quadrant
+  static_assert(NW == 4 || NW == 8, "four or eight epilogue warps");
+  constexpr int kSpan = 256 * 4 / NW;              // columns per warp
+  const int q = warp & 3;                          // tensor-memory lane quadrant
+  const int cbase = ((warp >> 2) - 1) * kSpan;     // warps 4-7: 0; warps 8-11: 128
   const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
   uint32_t k = 0;
   bool alive = true;
@@ -438,11 +460,7 @@ __device__ __forceinline__ void epilogue_role(const Params& P, Bars* bars, uint3
       const float c_next = last ? 0.0f : preload_coef(it + 1, nst, fs);
       const int row = 32 * q + lane;
       const bool vrow = row < ti.nA;
-      for (int cc = 0; cc < 256; cc += 32) {
-        uint32_t a[32], b[32];
-        TMEM_LD32(lane_addr + cc, a);
-        if (!first) TMEM_LD32(lane_addr + 256 + cc, b);
-        tmem_wait_ld();
+      auto chunk = [&](uint32_t* a, uint32_t* b, int cc) {
         if (last) {
           if (vrow) {
             double* orow = ti.out + (int64_t)(ti.row0 + row) * 2 * ti.m + ti.col0 + cc;
@@ -467,6 +485,28 @@ __device__ __forceinline__ void epilogue_role(const Params& P, Bars* bars, uint3
           }
           TMEM_ST32(lane_addr + 256 + cc, b);
           TMEM_ST32(lane_addr + cc, a);
+        }
+      };
+      if (NW == 8) {
+        for (int cc = cbase; cc < cbase + kSpan; cc += 64) {
+          uint32_t a0[32], b0[32], a1[32], b1[32];
+          TMEM_LD32(lane_addr + cc, a0);
+          TMEM_LD32(lane_addr + cc + 32, a1);
+          if (!first) {
+            TMEM_LD32(lane_addr + 256 + cc, b0);
+            TMEM_LD32(lane_addr + 256 + cc + 32, b1);
+          }
+          tmem_wait_ld();
+          chunk(a0, b0, cc);
+          chunk(a1, b1, cc + 32);
+        }
+      } else {
+        for (int cc = cbase; cc < cbase + kSpan; cc += 32) {
+          uint32_t a0[32], b0[32];
+          TMEM_LD32(lane_addr + cc, a0);
+          if (!first) TMEM_LD32(lane_addr + 256 + cc, b0);
+          tmem_wait_ld();
+          chunk(a0, b0, cc);
         }
       }
       tmem_wait_st();
@@ -571,7 +611,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_accumulate_kernel(const Params
     for (uint32_t i = 0; i < kWaitLimit && !mbar_try_wait(&bars->drain, 0); ++i) {
     }
   } else if (warp >= 4 && warp < 8) {
-    epilogue_role<stage_k<TF>()>(P, bars, tmem, warp, lane, fs);
+    epilogue_role<stage_k<TF>(), 4>(P, bars, tmem, warp, lane, fs);
   } else {
     // ------------------------------- converters -------------------------------
     const int cw = warp < 4 ? warp - 1 : warp - 5;   // 0 .. kConvWarps-1
@@ -838,7 +878,7 @@ tc_tma_kernel(const Params P, const __grid_constant__ CUtensorMap mapY,
         }
       }
   } else if (warp >= 4 && warp < 8) {
-    epilogue_role<kTmaStageK>(P, bars, tmem, warp, lane, fs);
+    epilogue_role<kTmaStageK, 4>(P, bars, tmem, warp, lane, fs);
   } else {
     // ------------------------------- converters -------------------------------
     const int cw = warp < 4 ? warp - 2 : warp - 6;   // 0 .. kConvWarpsT - 1
@@ -913,21 +953,110 @@ tc_tma_kernel(const Params P, const __grid_constant__ CUtensorMap mapY,
 }
 
 // ---------------------------------------------------------------------------------------------
+// Double-buffered accumulation for tc_op_kernel.  The MMA warp alternates between two 256-column
+// FP32 accumulators in tensor memory (buffer = global interval count & 1), so it never waits for
+// the drain of the interval it just finished.  The running FP32 sum of a work unit lives in the
+// registers of eight epilogue warps (warps 2-9: two per 32-lane quadrant, 128 columns each,
+// U[128] per thread) instead of in tensor memory.
+//
+// The rounding-bias correction keeps its form: interval 0 (the first stage alone) starts from
+// zero, interval i >= 1 from a preload d_i, about -1/2 of the partial sum it is expected to add,
+// written into its buffer when interval i - 2 (same buffer) is drained -- interval 1's, from
+// interval 0, in the drain of interval 0, which the MMA warp waits for once per unit.  The
+// preload is not recomputed at the next drain: the epilogue keeps U = sum of drained values -
+// sum of written preloads, i.e. at the drain of interval i with value V,
+//     s = U + V,  d = kappa_i s,  write d as interval i + 2's start,  U = s - d,
+// so that after the unit's last drain (no preload pending) U is the unit's sum.  Before the
+// drain U + V is the true running total minus the pending preload of interval i + 1, which
+// kappa_i accounts for when it turns s into the expected per-stage partial.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ int stages_through(int i, int nst, int fs) {
+  return i == 0 ? 1 : min(nst, 1 + i * fs);
+}
+__device__ __forceinline__ float db_kappa(int i, int nst, int fs) {
+  const float pending = (i >= 1) ? 0.5f * (float)interval_len(i + 1, nst, fs) : 0.0f;
+  // (at i = 0 interval 1's preload is written in the same drain, so nothing is pending yet)
+  return -0.5f * (float)interval_len(i + 2, nst, fs) /
+         ((float)stages_through(i, nst, fs) + pending);
+}
+
+__device__ __forceinline__ void epilogue_db_role(const Params& P, Bars* bars, uint32_t tmem,
+                                                 int warp, int lane, int fs) {
+  const int q = warp & 3;                          // tensor-memory lane quadrant
+  const int h = (warp - 2) >> 2;                   // warps 2-5: columns 0-127, 6-9: 128-255
+  const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(128 * h);
+  const int row = 32 * q + lane;
+  uint32_t k = 0;
+  bool alive = true;
+  float U[128];
+  for (int64_t u = blockIdx.x; u < P.nunits && alive; u += gridDim.x) {
+    const int64_t sa = (u / P.ntiles) * P.range_len;
+    const int64_t sb = min(P.ns, sa + P.range_len);
+    const int nst = (int)((sb - sa + kTmaStageK - 1) / kTmaStageK);
+    const int nint = interval_count(nst, fs);
+#pragma unroll
+    for (int i = 0; i < 128; ++i) U[i] = 0.0f;
+    for (int it = 0; it < nint; ++it, ++k) {
+      const uint32_t b = k & 1;
+      alive = mbar_wait(&bars->db_full[b], (k >> 1) & 1, bars, P.err, 13);
+      if (!alive) break;
+      tc_fence_after();
+      const bool pre = it + 2 < nint;
+      const float kap = pre ? db_kappa(it, nst, fs) : 0.0f;
+      // interval 1 starts from a preload too, formed from interval 0 (the MMA warp waits for
+      // this drain before interval 1): it goes into the other buffer
+      const bool pre1 = it == 0 && nint > 1;
+      const float kap1 = pre1 ? -0.5f * (float)interval_len(1, nst, fs) : 0.0f;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        uint32_t a[8], a1[8];
+        TMEM_LD8(lane_addr + b * 256 + 8 * c, a);
+        tmem_wait_ld();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float s = U[8 * c + i] + __uint_as_float(a[i]);
+          const float d = kap * s, d1 = kap1 * s;
+          U[8 * c + i] = (s - d) - d1;
+          a[i] = __float_as_uint(d);
+          a1[i] = __float_as_uint(d1);
+        }
+        if (pre) TMEM_ST8(lane_addr + b * 256 + 8 * c, a);
+        if (pre1) TMEM_ST8(lane_addr + (b ^ 1) * 256 + 8 * c, a1);
+      }
+      if (pre || pre1) tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars->db_empty[b]);
+      if (it != nint - 1) continue;
+      const TileInfo ti = decode_tile(P.tiles[u % P.ntiles], P.w != nullptr);
+      if (row < ti.nA) {
+        double* orow = ti.out + (int64_t)(ti.row0 + row) * 2 * ti.m + ti.col0 + 128 * h;
+        const int ncol = min(128, ti.nB - 128 * h);
+#pragma unroll
+        for (int i = 0; i < 128; ++i)
+          if (i < ncol) atomicAdd(orow + i, (double)U[i]);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // Prepared-operand variant (BF16X4): the operands were written to HBM once per sweep by the
 // preparation kernel (blm_prep.cu) in the tensor core's layout -- one 128-byte row per parameter
 // and 32-sample group holding [hi(32) | lo(32)] -- so this kernel only streams them: warp 1 loads
 // each stage's B rows (256 x 128 bytes) and, unless A is a view of B, its A rows (128 x 128
 // bytes) with 128-byte-swizzled cp.async.bulk.tensor into a four-deep ring; warp 0 issues the
-// four products of two K steps; warps 4-7 are the epilogue.  No converter warps.
+// four products of two K steps into one of two tensor-memory accumulators; warps 2-9 are the
+// epilogue (epilogue_db_role).  No converter warps.
 // ---------------------------------------------------------------------------------------------
 constexpr int kOpStagesP = 4;
 constexpr int kPStageBytes = (kBRows + kARows) * 128;          // 48 KB
 constexpr int kPBarOffset = kOpStagesP * kPStageBytes;          // 192 KB
 constexpr int kPSmemBytes = kPBarOffset + 256 + 1024;
-constexpr int kPThreads = 256;
+constexpr int kPThreads = 320;           // MMA, TMA, eight epilogue warps
 static_assert(kPSmemBytes <= 227 * 1024, "prepared-operand kernel exceeds shared memory");
 
-__global__ void __launch_bounds__(kPThreads, 1)
+__global__ void __maxnreg__(168)
 tc_op_kernel(const Params P, const __grid_constant__ CUtensorMap mapA,
              const __grid_constant__ CUtensorMap mapBS, const __grid_constant__ CUtensorMap mapBH) {
   extern __shared__ uint8_t smem_raw[];
@@ -941,8 +1070,10 @@ tc_op_kernel(const Params P, const __grid_constant__ CUtensorMap mapA,
       mbar_init(&bars->op_full[s], 1);
       mbar_init(&bars->op_empty[s], 1);
     }
-    mbar_init(&bars->l1_full, 1);
-    mbar_init(&bars->l1_empty, 4);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&bars->db_full[b], 1);
+      mbar_init(&bars->db_empty[b], 8);
+    }
     mbar_init(&bars->drain, 1);
     bars->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -973,9 +1104,14 @@ tc_op_kernel(const Params P, const __grid_constant__ CUtensorMap mapA,
         uint32_t acc = 1;
         const bool istart = (st == 0) || ((st - 1) % fs == 0);
         const bool iend = (st == 0) || ((st - 1) % fs == fs - 1) || (st == nst - 1);
+        const uint32_t dacc = tmem + (k & 1) * 256u;   // this interval's accumulator
         if (istart) {
-          alive = mbar_wait(&bars->l1_empty, (k & 1) ^ 1, bars, P.err, 11);
+          alive = mbar_wait(&bars->db_empty[k & 1], ((k >> 1) & 1) ^ 1, bars, P.err, 11);
           tc_fence_after();
+          // interval 0 of a unit starts from zero, later ones from the epilogue's preload;
+          // interval 1's preload comes from interval 0, so wait for that drain as well
+          if (alive && st == 1)
+            alive = mbar_wait(&bars->db_empty[(k - 1) & 1], ((k - 1) >> 1) & 1, bars, P.err, 14);
           acc = (st == 0) ? 0 : 1;
         }
         if (alive) alive = mbar_wait(&bars->op_full[slot], use & 1, bars, P.err, 12);
@@ -988,14 +1124,14 @@ tc_op_kernel(const Params P, const __grid_constant__ CUtensorMap mapA,
 #pragma unroll
           for (int ks = 0; ks < 2; ++ks) {
             const uint32_t o = ks * 32;
-            mma_bf16(tmem, sdesc(oa + o), sdesc(ob + o), acc);           // hi * hi
-            mma_bf16(tmem, sdesc(oa + o), sdesc(ob + 64 + o), 1);        // hi * lo
-            mma_bf16(tmem, sdesc(oa + 64 + o), sdesc(ob + o), 1);        // lo * hi
-            mma_bf16(tmem, sdesc(oa + 64 + o), sdesc(ob + 64 + o), 1);   // lo * lo
+            mma_bf16(dacc, sdesc(oa + o), sdesc(ob + o), acc);           // hi * hi
+            mma_bf16(dacc, sdesc(oa + o), sdesc(ob + 64 + o), 1);        // hi * lo
+            mma_bf16(dacc, sdesc(oa + 64 + o), sdesc(ob + o), 1);        // lo * hi
+            mma_bf16(dacc, sdesc(oa + 64 + o), sdesc(ob + 64 + o), 1);   // lo * lo
             acc = 1;
           }
           mma_commit(&bars->op_empty[slot]);
-          if (iend) mma_commit(&bars->l1_full);
+          if (iend) mma_commit(&bars->db_full[k & 1]);
         }
         __syncwarp();
         if (iend) ++k;
@@ -1040,8 +1176,8 @@ tc_op_kernel(const Params P, const __grid_constant__ CUtensorMap mapA,
              ++i) {
         }
       }
-  } else if (warp >= 4 && warp < 8) {
-    epilogue_role<kTmaStageK>(P, bars, tmem, warp, lane, fs);
+  } else if (warp >= 2 && warp < 10) {
+    epilogue_db_role(P, bars, tmem, warp, lane, fs);
   }
 
   tc_fence_before();

@@ -70,7 +70,7 @@ def test_driver_on_gpu_follows_the_oracle_loop():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     toy = T.make_toy()
-    kw = dict(n_iter=10, n_old=2, adaptive=False)
+    kw = dict(n_iter=15, n_old=2, adaptive=False)
     ref = driver.optimize(lambda mu: T.exact(toy, mu), np.zeros(toy.n), OFFS, 1,
                           step_fn=oracle_step, **kw)
     got = driver.optimize(lambda mu: T.exact(toy, mu), np.zeros(toy.n), OFFS, 1, **kw)
