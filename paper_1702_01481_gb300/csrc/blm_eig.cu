@@ -143,6 +143,8 @@ __device__ __forceinline__ double to_double(dw x) { return (double)x.hi + (doubl
 __device__ __forceinline__ double to_double(double x) { return x; }
 __device__ __forceinline__ float mag(dw x) { return fabsf(x.hi); }
 __device__ __forceinline__ double mag(double x) { return fabs(x); }
+__device__ __forceinline__ double to_double(float x) { return (double)x; }
+__device__ __forceinline__ float mag(float x) { return fabsf(x); }
 __device__ __forceinline__ dw dw_abs(dw x) { return x.hi < 0.0f ? -x : x; }
 __device__ __forceinline__ dw dw_scale(dw x, float p2) { return dw{x.hi * p2, x.lo * p2}; }  // p2 = 2^k
 
@@ -260,6 +262,11 @@ __device__ void house3f(float x, float y, float z, float& beta, float& v1, float
   v2 = z / v0;
   beta = 1.0f + fabsf(x) / mu;
   alpha = -sg * mu;
+}
+
+__device__ __forceinline__ void house3(float x, float y, float z, float& beta, float& v1,
+                                       float& v2, float& alpha) {
+  house3f(x, y, z, beta, v1, v2, alpha);
 }
 
 // Eigenvalues of the n x n (n <= 8) Hessenberg matrix h (row-major, leading dimension 8), in
@@ -415,6 +422,11 @@ template <>
 struct QrArith<double> {
   static constexpr double kEps = 2.220446049250313e-16;   // deflation threshold (relative)
   __device__ static double of(double d) { return d; }
+};
+template <>
+struct QrArith<float> {
+  static constexpr double kEps = 3.0e-7;                  // about five FP32 units in the last place
+  __device__ static float of(double d) { return (float)d; }
 };
 template <>
 struct QrArith<dw> {
@@ -1310,15 +1322,31 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
   const int want = pb.mode == 1 ? 1 : pb.k;
   EIG_MARK(3);
   // ---- 4. all eigenvalues: QR in double words; FP64 if that fails ----
-  dw* Wd = reinterpret_cast<dw*>(W);
-  for (int64_t idx = t; idx < mm; idx += nt) Wd[idx] = dw_of_double(Hh[idx] * gscale);
-  if (t == 0) sh.iscal[5] = 1;
-  __syncthreads();
-  bool ok = hqr_windowed<dw>(Wd, m, wr, wi, anorm * gscale, dsm, sh);
-  __syncthreads();
-  for (int i = t; i < m; i += nt)
-    if (!isfinite(wr[i]) || !isfinite(wi[i])) sh.iscal[5] = 0;
-  __syncthreads();
+  bool ok = false;
+  if (pb.fp32_locate) {
+    // a well-conditioned small problem (the Davidson projection): FP32 only locates the
+    // eigenvalues; each kept one is recomputed in FP64 by inverse iteration below
+    float* Wf = reinterpret_cast<float*>(W);
+    for (int64_t idx = t; idx < mm; idx += nt) Wf[idx] = (float)(Hh[idx] * gscale);
+    if (t == 0) sh.iscal[5] = 1;
+    __syncthreads();
+    ok = hqr_windowed<float>(Wf, m, wr, wi, anorm * gscale, dsm, sh);
+    __syncthreads();
+    for (int i = t; i < m; i += nt)
+      if (!isfinite(wr[i]) || !isfinite(wi[i])) sh.iscal[5] = 0;
+    __syncthreads();
+  }
+  if (!ok || sh.iscal[5] == 0 || !pb.fp32_locate) {
+    dw* Wd = reinterpret_cast<dw*>(W);
+    for (int64_t idx = t; idx < mm; idx += nt) Wd[idx] = dw_of_double(Hh[idx] * gscale);
+    if (t == 0) sh.iscal[5] = 1;
+    __syncthreads();
+    ok = hqr_windowed<dw>(Wd, m, wr, wi, anorm * gscale, dsm, sh);
+    __syncthreads();
+    for (int i = t; i < m; i += nt)
+      if (!isfinite(wr[i]) || !isfinite(wi[i])) sh.iscal[5] = 0;
+    __syncthreads();
+  }
   if (!ok || sh.iscal[5] == 0) {
 #ifdef BLM_EIG_DEBUG
     if (t == 0) printf("eig: problem %d double-word QR failed, FP64 QR\n", (int)blockIdx.x);
@@ -1699,6 +1727,7 @@ davidson_kernel(const EigProblem* __restrict__ probs, double tol, int max_iter, 
   extern __shared__ double dsm[];
   __shared__ Shared sh;
   __shared__ double hk[kDavMax * kDavMax];
+  __shared__ double coef[kDavMax];
   __shared__ int bar_ok;
   const EigProblem pb = probs[0];
   const int m = pb.m;
@@ -1789,13 +1818,29 @@ davidson_kernel(const EigProblem* __restrict__ probs, double tol, int max_iter, 
 #ifdef BLM_EIG_TIMING
     dits = it + 1;
 #endif
-    // projected matrix: only the newest row and column change between restarts
-    for (int i = 0; i < k; ++i) {
-      const bool newer = (i == k - 1);
-      for (int j = 0; j < k; ++j) {
-        if (!fresh && !newer && j != k - 1) continue;
-        const double v = dotv(V + (int64_t)i * m, HV + (int64_t)j * m, m, sh);
-        if (t == 0) hk[i * kDavMax + j] = v;
+    // projected matrix: only the newest row and column change between restarts; one warp per
+    // dot product, all of them between two barriers
+    {
+      const int np = fresh ? k * k : 2 * k - 1;
+      const int lane = t & 31, wid = t >> 5, nw = nt >> 5;
+      for (int q = wid; q < np; q += nw) {
+        int i, j;
+        if (fresh) {
+          i = q / k;
+          j = q - i * k;
+        } else if (q < k) {
+          i = k - 1;   // the new row
+          j = q;
+        } else {
+          i = q - k;   // the new column, rows above the new row
+          j = k - 1;
+        }
+        const double* vi = V + (int64_t)i * m;
+        const double* hj = HV + (int64_t)j * m;
+        double acc = 0.0;
+        for (int e = lane; e < m; e += 32) acc = fma(vi[e], hj[e], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) hk[i * kDavMax + j] = acc;
       }
     }
     __syncthreads();
@@ -1808,7 +1853,7 @@ davidson_kernel(const EigProblem* __restrict__ probs, double tol, int max_iter, 
     if (t == 0) *sStat = ST_OK;
     __syncthreads();
     DAV_T(0);
-    EigProblem sp{k, 1, 0, 0, sS, sH, sW, sLam, sVec, sStat};
+    EigProblem sp{k, 1, 0, 1, sS, sH, sW, sLam, sVec, sStat};
     dense_geig(sp, dsm, sh);
     __syncthreads();
     DAV_T(1);
@@ -1859,12 +1904,25 @@ davidson_kernel(const EigProblem* __restrict__ probs, double tol, int max_iter, 
       tv[i] = -r[i] / den;
     }
     __syncthreads();
-    for (int pass = 0; pass < 2; ++pass)
-      for (int j = 0; j < k; ++j) {
-        const double c = dotv(SV + (int64_t)j * m, tv, m, sh);
-        for (int i = t; i < m; i += nt) tv[i] -= c * V[(int64_t)j * m + i];
-        __syncthreads();
+    // classical Gram-Schmidt in the S inner product, twice: the k coefficients by one warp each,
+    // then one combined update
+    for (int pass = 0; pass < 2; ++pass) {
+      const int lane = t & 31, wid = t >> 5, nw = nt >> 5;
+      for (int j = wid; j < k; j += nw) {
+        const double* sj = SV + (int64_t)j * m;
+        double acc = 0.0;
+        for (int e = lane; e < m; e += 32) acc = fma(sj[e], tv[e], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) coef[j] = acc;
       }
+      __syncthreads();
+      for (int i = t; i < m; i += nt) {
+        double x = tv[i];
+        for (int j = 0; j < k; ++j) x -= coef[j] * V[(int64_t)j * m + i];
+        tv[i] = x;
+      }
+      __syncthreads();
+    }
     double* stv = SV + (int64_t)k * m;
     double* htv = HV + (int64_t)k * m;
     DAV_T(3);

@@ -152,7 +152,7 @@ struct EigProblem {
   int32_t m;           // dimension (1 + tangent)
   int32_t k;           // directions wanted (lowest real parts)
   int32_t mode;        // 0: block (complex pair -> Re, Im), 1: combined (lowest must be real)
-  int32_t pad;
+  int32_t fp32_locate; // 1: locate eigenvalues with an FP32 QR (well-conditioned small problems)
   const double* S;     // m x m row-major
   const double* H;     // m x m row-major
   double* work;        // 5 m^2 + 16 m doubles

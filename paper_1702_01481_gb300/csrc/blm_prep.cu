@@ -255,6 +255,132 @@ prep_kernel(const PrepArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// The same preparation with the tiles read straight into registers (16-byte rows aligned):
+// no shared-memory staging and no barriers in the loop, so occupancy is set by registers alone
+// (four CTAs of 128 threads per SM instead of three) and each thread keeps its tile's sixteen
+// 16-byte loads in flight.  The FP64 partial sums live in a per-thread shared-memory slot.
+// ---------------------------------------------------------------------------------------------
+constexpr int kPdThreads = 128;
+
+template <bool WT>
+__global__ void __launch_bounds__(kPdThreads, 4)
+prep_direct_kernel(const PrepArgs a) {
+  __shared__ double dsum[kPdThreads * 12];   // per thread: sY[4], sEY[4], sZ[4]; then reduction
+  const int t = threadIdx.x;
+  const int p4 = t & 15, sb = t >> 4;
+  const int64_t p0 = (int64_t)blockIdx.x * kPrepP;
+  const int64_t pq = p0 + 4 * p4;                      // this thread's first parameter
+  const int64_t sbase = (int64_t)blockIdx.y * kPrepT * kPrepTiles;
+  const int ntiles = (int)min((int64_t)kPrepTiles, (a.ns - sbase + kPrepT - 1) / kPrepT);
+  const int nval = (int)max((int64_t)0, min((int64_t)4, a.n - pq));   // valid parameters
+  float c[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) c[e] = (a.shift && e < nval) ? __ldg(a.shift + pq + e) : 0.0f;
+  double* my = dsum + t * 12;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) my[i] = 0.0;
+  float fY[4] = {0, 0, 0, 0}, fEY[4] = {0, 0, 0, 0}, fZ[4] = {0, 0, 0, 0};
+  double dW = 0.0, dWE = 0.0;
+  const bool scal_thread = a.scal && blockIdx.x == 0 && p4 == 0;
+
+  for (int ti = 0; ti < ntiles; ++ti) {
+    const int64_t s0 = sbase + (int64_t)ti * kPrepT + 8 * sb;   // this thread's 8 samples
+    float4 o[8], g[8];
+    float ev[8], wv[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int64_t s = s0 + j;
+      const bool ok = s < a.ns;
+      o[j] = g[j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if (ok && nval == 4) {
+        o[j] = __ldcs(reinterpret_cast<const float4*>(a.Y + s * a.ld + pq));
+        g[j] = __ldcs(reinterpret_cast<const float4*>(a.Z + s * a.ld + pq));
+      } else if (ok) {   // the last, partial quad of parameters
+        const float* yr = a.Y + s * a.ld + pq;
+        const float* zr = a.Z + s * a.ld + pq;
+        o[j] = make_float4(nval > 0 ? yr[0] : 0.0f, nval > 1 ? yr[1] : 0.0f, nval > 2 ? yr[2] : 0.0f, 0.0f);
+        g[j] = make_float4(nval > 0 ? zr[0] : 0.0f, nval > 1 ? zr[1] : 0.0f, nval > 2 ? zr[2] : 0.0f, 0.0f);
+      }
+      ev[j] = ok ? __ldg(a.E + s) : 0.0f;
+      wv[j] = ok ? (WT ? __ldg(a.w + s) : 1.0f) : 0.0f;
+    }
+    float ya[4][8], xb[4][8], yb[WT ? 4 : 1][8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (scal_thread) {
+        dW += (double)wv[j];
+        dWE += (double)(wv[j] * ev[j]);
+      }
+      const float ov[4] = {o[j].x, o[j].y, o[j].z, o[j].w}, gv[4] = {g[j].x, g[j].y, g[j].z, g[j].w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float y = (s0 + j < a.ns) ? ov[e] - c[e] : 0.0f;
+        const float wy = wv[j] * y;
+        ya[e][j] = y;
+        if (WT) yb[WT ? e : 0][j] = wy;
+        xb[e][j] = wv[j] * fmaf(ev[j], y, gv[e]);
+        fY[e] += wy;
+        fEY[e] = fmaf(wy, ev[j], fEY[e]);
+        fZ[e] = fmaf(wv[j], gv[e], fZ[e]);
+      }
+    }
+    const int64_t s0t = sbase + (int64_t)ti * kPrepT;
+    const int64_t grp = s0t / 32 + (sb >> 2);
+    const int chunk = sb & 3;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (e >= nval) continue;
+      const int64_t off = (pq + e) * a.row_bytes + grp * 128 + 16 * chunk;
+      uint4 hi, lo;
+      split8_bf16(ya[e], hi, lo);
+      *reinterpret_cast<uint4*>(a.opA + off) = hi;
+      *reinterpret_cast<uint4*>(a.opA + off + 64) = lo;
+      split8_bf16(xb[e], hi, lo);
+      *reinterpret_cast<uint4*>(a.opBH + off) = hi;
+      *reinterpret_cast<uint4*>(a.opBH + off + 64) = lo;
+      if (WT) {
+        split8_bf16(yb[WT ? e : 0], hi, lo);
+        *reinterpret_cast<uint4*>(a.opBS + off) = hi;
+        *reinterpret_cast<uint4*>(a.opBS + off + 64) = lo;
+      }
+    }
+    if ((ti + 1) % kPrepRun == 0 || ti + 1 == ntiles) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        my[e] += (double)fY[e];
+        my[4 + e] += (double)fEY[e];
+        my[8 + e] += (double)fZ[e];
+        fY[e] = fEY[e] = fZ[e] = 0.0f;
+      }
+    }
+  }
+  if (a.sY) {
+    // the 8 sample blocks of a parameter quad: threads p4 + 16 sb, sb = 0..7
+    __syncthreads();
+    if (t < kPrepP) {
+      const int q = t >> 2, e = t & 3;
+      double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      for (int b8 = 0; b8 < 8; ++b8) {
+        const double* src = dsum + (q + 16 * b8) * 12;
+        s1 += src[e];
+        s2 += src[4 + e];
+        s3 += src[8 + e];
+      }
+      const int64_t p = p0 + t;
+      if (p < a.n) {
+        atomicAdd(a.sY + p, s1);
+        atomicAdd(a.sEY + p, s2);
+        atomicAdd(a.sZ + p, s3);
+      }
+    }
+  }
+  if (scal_thread) {
+    atomicAdd(a.scal + 0, dW);
+    atomicAdd(a.scal + 1, dWE);
+  }
+}
+
 }  // namespace
 
 void launch_prep(const float* Y, const float* Z, const float* E, const float* w, int64_t ns,
@@ -272,7 +398,12 @@ void launch_prep(const float* Y, const float* Z, const float* E, const float* w,
              (ld % 4 == 0) && ((((uintptr_t)Y) | ((uintptr_t)Z)) % 16 == 0) ? 1 : 0};
   dim3 grid((unsigned)((n + kPrepP - 1) / kPrepP),
             (unsigned)((ns + kPrepT * kPrepTiles - 1) / (kPrepT * kPrepTiles)));
-  prep_kernel<<<grid, kPrepThreads, kPrepSmem, st>>>(a);
+  if (a.vec && w)
+    prep_direct_kernel<true><<<grid, kPdThreads, 0, st>>>(a);
+  else if (a.vec)
+    prep_direct_kernel<false><<<grid, kPdThreads, 0, st>>>(a);
+  else
+    prep_kernel<<<grid, kPrepThreads, kPrepSmem, st>>>(a);
 }
 
 }  // namespace blm

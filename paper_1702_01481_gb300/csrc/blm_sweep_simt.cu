@@ -413,7 +413,7 @@ project_tiled_kernel(const T* __restrict__ O, const T* __restrict__ G, int64_t l
 // parameters of one sample feeds 80 products and every direction load is a broadcast.  The
 // products use paired FP32 FMAs (fma.rn.f32x2: two independent round-to-nearest FMAs, bit for
 // bit the scalar ones, so the sums equal project_tiled_kernel's).  Runs of 16 parameters are
-// staged by 16-byte cp.async, three stages in flight; sample rows are 64 bytes with their four
+// staged by 16-byte cp.async, double-buffered; sample rows are 64 bytes with their four
 // 16-byte chunks XOR-swizzled by bits 1-2 of the row, so that the eight rows of a quarter-warp
 // load, and the eight chunks of a quarter-warp's copies, fall in different bank groups.
 // ---------------------------------------------------------------------------------------------
@@ -421,7 +421,7 @@ constexpr int kRbThreads = 128;
 constexpr int kRbS = 256;       // samples per CTA
 constexpr int kRbC = 16;        // parameters per stage
 constexpr int kRbJ = 20;        // directions per thread
-constexpr int kRbStages = 3;
+constexpr int kRbStages = 2;     // 68 KB: three CTAs (12 warps) per SM
 constexpr int kRbTile = kRbS * kRbC;                       // floats of one O or G stage
 constexpr int kRbStage = 2 * kRbTile + kRbC * kRbJ + kRbC;  // O, G, D [c][j], shift
 constexpr size_t kRbSmem = sizeof(float) * kRbStages * kRbStage;
@@ -445,7 +445,7 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, int bytes
                : "memory");
 }
 
-__global__ void __launch_bounds__(kRbThreads, 2)
+__global__ void __launch_bounds__(kRbThreads, 3)
 project_rb_kernel(const float* __restrict__ O, const float* __restrict__ G, int64_t ld,
                   const float* __restrict__ shift32, const ProjBlock* __restrict__ blocks,
                   const double* __restrict__ cen, float* __restrict__ Y, float* __restrict__ Z,
@@ -494,10 +494,9 @@ project_rb_kernel(const float* __restrict__ O, const float* __restrict__ G, int6
 
   const int rbase = (warp & 1) * 128 + lane;
   issue(0);
-  issue(1);
   for (int r = 0; r < nruns; ++r) {
-    issue(r + 2);
-    asm volatile("cp.async.wait_group 2;" ::: "memory");
+    issue(r + 1);
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
     __syncthreads();
     const float* stg = rb_smem + (r % kRbStages) * kRbStage;
     const float* tile = stg + (isO ? 0 : kRbTile);
