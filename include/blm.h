@@ -21,7 +21,8 @@
  *
  * Conventions
  *   - Sample arrays may be device memory or host memory (pinned or pageable); host arrays are
- *     copied through the handle's staging buffers.  Element type per blm_problem.input_type.
+ *     copied through the handle's two staging buffers (256 MiB each, allocated on the
+ *     handle's first host-memory call).  Element type per blm_problem.input_type.
  *   - All calls are asynchronous on the handle's stream; results are valid once it syncs.
  *   - The handle owns every accumulator and workspace it needs (allocated in blm_create).
  *   - Call order is enforced: accumulate+ -> block_solve -> project+ -> combined_solve;

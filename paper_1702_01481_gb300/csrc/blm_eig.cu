@@ -1099,27 +1099,66 @@ __device__ void warp_back_transform(const double* Rt, const double* hbeta, const
   } while (0)
 #endif
 
-// Row kernels of the dense reductions, one warp per row, lanes over columns.  The restrict
-// qualifiers tell the compiler that the row and the vector do not overlap, so it can issue the
-// loads of several columns before the stores of earlier ones: the rows live in L2 and a loop
-// that waits for each store runs at L2 latency.
-// a[j] -= s * x[j], j = j0 + lane, j0 + lane + 32, ... < j1
-__device__ __forceinline__ void row_axpy(double* __restrict__ a, const double* __restrict__ x,
-                                         double s, int j0, int j1, int lane) {
-#pragma unroll 4
-  for (int j = j0 + lane; j < j1; j += 32) a[j] -= s * x[j];
-}
-// sum over j of a[j] * x[j] (this lane's part)
-__device__ __forceinline__ double row_dot(const double* __restrict__ a, const double* __restrict__ x,
-                                          int j0, int j1, int lane) {
-  double s0 = 0.0, s1 = 0.0;
-  int j = j0 + lane;
-  for (; j + 32 < j1; j += 64) {
-    s0 = fma(a[j], x[j], s0);
-    s1 = fma(a[j + 32], x[j + 32], s1);
+// Row kernels of the dense reductions, one warp per four rows, lanes over columns.
+// Four rows i_r = i0 + r * stride (those below iend) of a row-major matrix with leading
+// dimension ld, by one warp: a_i[j] -= s_r * x[j] for j in [j0, j1_r).  The matrices live in
+// global memory (L2), so each 128-column chunk's loads of all four rows are issued before any
+// store: sixteen loads in flight per lane instead of the four of a single row.
+__device__ __forceinline__ void rows4_axpy(double* a, int64_t ld, int i0, int stride, int iend,
+                                           const double* s, const int* j1, const double* x,
+                                           int j0, int lane) {
+  int jmax = j0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+    if (i0 + r * stride < iend) jmax = max(jmax, j1[r]);
+  for (int jc = j0 + lane; jc < jmax; jc += 128) {
+    double v[4][4], xv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) xv[q] = (jc + 32 * q < jmax) ? x[jc + 32 * q] : 0.0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = i0 + r * stride, j = jc + 32 * q;
+        v[r][q] = (i < iend && j < j1[r]) ? a[(int64_t)i * ld + j] : 0.0;
+      }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = i0 + r * stride, j = jc + 32 * q;
+        if (i < iend && j < j1[r]) a[(int64_t)i * ld + j] = v[r][q] - s[r] * xv[q];
+      }
   }
-  if (j < j1) s0 = fma(a[j], x[j], s0);
-  return s0 + s1;
+}
+
+// The same four rows: z_r = a_i . x over [j0, j1), then a_i[j] -= beta z_r x[j].
+__device__ __forceinline__ void rows4_dot_axpy(double* a, int64_t ld, int i0, int stride, int iend,
+                                               const double* x, double beta, int j0, int j1,
+                                               int lane) {
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int jc = j0 + lane; jc < j1; jc += 128) {
+    double xv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) xv[q] = (jc + 32 * q < j1) ? x[jc + 32 * q] : 0.0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = i0 + r * stride, j = jc + 32 * q;
+        const double v = (i < iend && j < j1) ? a[(int64_t)i * ld + j] : 0.0;
+        acc[r] = fma(v, xv[q], acc[r]);
+      }
+  }
+  double sc[4];
+  int j1r[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+    sc[r] = beta * acc[r];
+    j1r[r] = j1;
+  }
+  rows4_axpy(a, ld, i0, stride, iend, sc, j1r, x, j0, lane);
 }
 
 // Dense solver for one problem, run by the whole CTA (dsm: up to 200 KB of shared memory).
@@ -1202,7 +1241,17 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
       col[i] = v;
     }
     __syncthreads();
-    for (int i = k + 1 + rw; i < m; i += rnw) row_axpy(L + (int64_t)i * m, col, col[i], k + 1, i + 1, rl);
+    for (int i = k + 1 + rw; i < m; i += 4 * rnw) {
+      double sv[4];
+      int j1[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int ir = i + r * rnw;
+        sv[r] = ir < m ? col[ir] : 0.0;
+        j1[r] = ir + 1;
+      }
+      rows4_axpy(L, m, i, rnw, m, sv, j1, col, k + 1, rl);
+    }
     __syncthreads();
   }
   if (sh.iscal[1] != ST_OK) {
@@ -1218,8 +1267,17 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
       col[j] = v;
     }
     __syncthreads();
-    for (int i = k + 1 + rw; i < m; i += rnw)
-      row_axpy(A + (int64_t)i * m, col, L[(int64_t)i * m + k], 0, m, rl);
+    for (int i = k + 1 + rw; i < m; i += 4 * rnw) {
+      double sv[4];
+      int j1[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int ir = i + r * rnw;
+        sv[r] = ir < m ? L[(int64_t)ir * m + k] : 0.0;
+        j1[r] = m;
+      }
+      rows4_axpy(A, m, i, rnw, m, sv, j1, col, 0, rl);
+    }
     __syncthreads();
   }
   // ---- 2c. A <- A L^-T (column forward substitution) ----
@@ -1232,7 +1290,17 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
       vtmp[i] = L[(int64_t)i * m + k];            // column k of L, read once
     }
     __syncthreads();
-    for (int i = rw; i < m; i += rnw) row_axpy(A + (int64_t)i * m, vtmp, col[i], k + 1, m, rl);
+    for (int i = rw; i < m; i += 4 * rnw) {
+      double sv[4];
+      int j1[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int ir = i + r * rnw;
+        sv[r] = ir < m ? col[ir] : 0.0;
+        j1[r] = m;
+      }
+      rows4_axpy(A, m, i, rnw, m, sv, j1, vtmp, k + 1, rl);
+    }
     __syncthreads();
   }
   EIG_MARK(2);
@@ -1290,15 +1358,20 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
         vtmp[j] = beta * sum;
       }
       __syncthreads();
-      for (int i = k + 1 + rw; i < m; i += rnw) row_axpy(A + (int64_t)i * m, vtmp, col[i], k, m, rl);
+      for (int i = k + 1 + rw; i < m; i += 4 * rnw) {
+        double sv[4];
+        int j1[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int ir = i + r * rnw;
+          sv[r] = ir < m ? col[ir] : 0.0;
+          j1[r] = m;
+        }
+        rows4_axpy(A, m, i, rnw, m, sv, j1, vtmp, k, rl);
+      }
       __syncthreads();
       // right: all rows, columns k+1.. (warp per row)
-      const int lane = t & 31, wid = t >> 5, nw = nt >> 5;
-      for (int i = wid; i < m; i += nw) {
-        double zi = row_dot(A + (int64_t)i * m, col, k + 1, m, lane);
-        for (int o = 16; o > 0; o >>= 1) zi += __shfl_xor_sync(0xffffffffu, zi, o);
-        row_axpy(A + (int64_t)i * m, col, zi * beta, k + 1, m, lane);
-      }
+      for (int i = rw; i < m; i += 4 * rnw) rows4_dot_axpy(A, m, i, rnw, m, col, beta, k + 1, m, rl);
       __syncthreads();
     }
     // store the reflector below the subdiagonal
@@ -1626,18 +1699,6 @@ eig_kernel(const EigProblem* __restrict__ probs) {
 // Converged when ||H u - theta S u|| <= tol * ||S u|| * max(1, |theta|).
 // ---------------------------------------------------------------------------------------------
 constexpr int kDavMax = 40;
-
-__device__ void matvec(const double* M, int m, const double* x, double* y) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = wid; i < m; i += nw) {
-    const double* row = M + (int64_t)i * m;
-    double s = 0.0;
-    for (int j = lane; j < m; j += 32) s = fma(row[j], x[j], s);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) y[i] = s;
-  }
-  __syncthreads();
-}
 
 __device__ double dotv(const double* a, const double* b, int m, Shared& sh) {
   double p = 0.0;
