@@ -278,6 +278,32 @@ def run_ours(args, rank, world):
                             "solve_ms": round(solves, 1),
                             "speedup_mixed_over_fp64": round(scaled / ms_step, 2)}
         s64.close()
+        # "+hist": the same FP64 step with N_O = 3 history directions (seeded unit rows), which
+        # adds the Theta projections and their sums (Eq. 9-10) to the first sweep
+        import numpy as np
+        n_old = 3
+        rng = np.random.default_rng(12345)
+        D = rng.standard_normal((n_old, n))
+        D /= np.linalg.norm(D, axis=1, keepdims=True)
+        sh = blm.Step(n, wl.block_offsets, wl.n_keep, n_old=n_old, old_dirs=D,
+                      stream=stream.cuda_stream)
+        blm.blm_profile(sh.h, 1)
+        torch.cuda.synchronize()
+        t0.record(stream)
+        sh.accumulate(O64, G64, E64)
+        sh.block_solve()
+        sh.project(O64, G64, E64)
+        sh.combined_solve(d64)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ph = blm.blm_profile_read(sh.h)
+        total_h = t0.elapsed_time(t1)
+        sweeps_h = sum(ph[k][0] for k in ("reference_shift", "first_moments", "contract_f64",
+                                           "project", "history_terms"))
+        res["fp64_hist"] = {"n_old": n_old, "measured_samples": c, "measured_ms": round(total_h, 1),
+                            "history_terms_ms": round(ph["history_terms"][0], 1),
+                            "ms_per_step_scaled": round(sweeps_h * (ns / c) + (total_h - sweeps_h), 1)}
+        sh.close()
     return res
 
 
@@ -443,6 +469,8 @@ def main():
         line["tc_pass1"] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in res["tc_pass1"].items()}
     if "fp64_path" in res:
         line["fp64_path"] = res["fp64_path"]
+    if "fp64_hist" in res:
+        line["fp64_hist"] = res["fp64_hist"]
     if not args.no_e2e and world == 1:
         line["e2e"] = run_e2e(args)
     else:

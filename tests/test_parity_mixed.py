@@ -134,6 +134,17 @@ def test_combined_sums_of_256_directions(torch_cuda):
     check(got, ref, O, G, E, None, wl.block_offsets, wl.n_keep)
 
 
+def test_more_than_20_directions_per_block(torch_cuda):
+    """8 blocks of 64 with K = 24: more directions per block than the register-blocked
+    projection holds (20), so the second sweep takes the 2 x 8-direction projection kernel."""
+    wl = synth.Workload("t", 512, 4096, synth.equal_blocks(512, 8), 24, decades=4.0, chunk=4096,
+                        seed=9)
+    O, G, E = f32_inputs(wl)
+    ref = oracle_f32(O, G, E, None, wl.block_offsets, wl.n_keep)
+    got = run_mixed(torch_cuda, O, G, E, None, wl.block_offsets, wl.n_keep, chunks=[1500, 2596])
+    check(got, ref, O, G, E, None, wl.block_offsets, wl.n_keep)
+
+
 @pytest.mark.parametrize("which", ["n200", "blocks256"])
 def test_tf32_split_precision(torch_cuda, which):
     """The TF32 hi/lo split (2^-22 operand representation): same checks, with the matrix and
