@@ -807,6 +807,11 @@ blm_status blm_create(const blm_problem* p, void* stream, blm_handle** out) {
     };
     for (int b = 0; b < h->nb; ++b) add(t1, h->off[b], h->Mb[b], h->d_C + h->C_off[b]);
     add(t2, 0, (int)h->dc, h->d_Cc);
+    // the combined overlap is symmetric and assembled from its upper triangle: overlap tiles
+    // wholly below the diagonal (last column < first row) are not computed
+    t2.erase(std::remove_if(t2.begin(), t2.end(),
+                            [](const TcTile& t) { return t.col0 < t.m && t.col0 + 256 <= t.row0; }),
+             t2.end());
     h->ntc1 = (int)t1.size();
     h->ntc2 = (int)t2.size();
     auto aligned = [](const std::vector<TcTile>& v) {

@@ -141,9 +141,11 @@ __global__ void assemble_combined_kernel(int64_t dc, const double* C, const doub
       const int64_t a = ai - 1, c = ci - 1;
       const double ma = sY[a] * iw, mc = sY[c] * iw;
       const double maE = sEY[a] * iw, yc = (sEY[c] + sZ[c]) * iw;
-      const double ac = C[a * 2 * dc + c] * iw, ca = C[c * 2 * dc + a] * iw;
+      // upper triangle only (the tensor-core path does not compute overlap tiles wholly below
+      // the diagonal)
+      const double su = (a <= c ? C[a * 2 * dc + c] : C[c * 2 * dc + a]) * iw;
       const double ay = C[a * 2 * dc + dc + c] * iw;
-      s = 0.5 * (ac + ca) - ma * mc;
+      s = su - ma * mc;
       hv = ay - ma * yc - mc * (maE - ma * Em);
       if (shift != 0.0 && gram) hv += shift * gram[a * dc + c];
     }
