@@ -1099,7 +1099,29 @@ __device__ void warp_back_transform(const double* Rt, const double* hbeta, const
   } while (0)
 #endif
 
-// Row kernels of the dense reductions, one warp per four rows, lanes over columns.
+// Row kernels of the dense reductions, lanes over columns.  Small matrices (the Davidson
+// projection, m <= 64) go one row per warp; larger ones four rows per warp (below).
+// a[j] -= s * x[j], j = j0 + lane, j0 + lane + 32, ... < j1
+__device__ __forceinline__ void row_axpy(double* __restrict__ a, const double* __restrict__ x,
+                                         double s, int j0, int j1, int lane) {
+#pragma unroll 4
+  for (int j = j0 + lane; j < j1; j += 32) a[j] -= s * x[j];
+}
+// sum over j of a[j] * x[j] (this lane's part)
+__device__ __forceinline__ double row_dot(const double* __restrict__ a, const double* __restrict__ x,
+                                          int j0, int j1, int lane) {
+  double s0 = 0.0, s1 = 0.0;
+  int j = j0 + lane;
+  for (; j + 32 < j1; j += 64) {
+    s0 = fma(a[j], x[j], s0);
+    s1 = fma(a[j + 32], x[j + 32], s1);
+  }
+  if (j < j1) s0 = fma(a[j], x[j], s0);
+  return s0 + s1;
+}
+constexpr int kRows4Min = 64;   // matrices larger than this use the four-row kernels
+
+// Four-row kernels.
 // Four rows i_r = i0 + r * stride (those below iend) of a row-major matrix with leading
 // dimension ld, by one warp: a_i[j] -= s_r * x[j] for j in [j0, j1_r).  The matrices live in
 // global memory (L2), so each 128-column chunk's loads of all four rows are issued before any
@@ -1241,16 +1263,21 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
       col[i] = v;
     }
     __syncthreads();
-    for (int i = k + 1 + rw; i < m; i += 4 * rnw) {
-      double sv[4];
-      int j1[4];
+    if (m <= kRows4Min) {
+      for (int i = k + 1 + rw; i < m; i += rnw)
+        row_axpy(L + (int64_t)i * m, col, col[i], k + 1, i + 1, rl);
+    } else {
+      for (int i = k + 1 + rw; i < m; i += 4 * rnw) {
+        double sv[4];
+        int j1[4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int ir = i + r * rnw;
-        sv[r] = ir < m ? col[ir] : 0.0;
-        j1[r] = ir + 1;
+        for (int r = 0; r < 4; ++r) {
+          const int ir = i + r * rnw;
+          sv[r] = ir < m ? col[ir] : 0.0;
+          j1[r] = ir + 1;
+        }
+        rows4_axpy(L, m, i, rnw, m, sv, j1, col, k + 1, rl);
       }
-      rows4_axpy(L, m, i, rnw, m, sv, j1, col, k + 1, rl);
     }
     __syncthreads();
   }
@@ -1267,16 +1294,21 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
       col[j] = v;
     }
     __syncthreads();
-    for (int i = k + 1 + rw; i < m; i += 4 * rnw) {
-      double sv[4];
-      int j1[4];
+    if (m <= kRows4Min) {
+      for (int i = k + 1 + rw; i < m; i += rnw)
+        row_axpy(A + (int64_t)i * m, col, L[(int64_t)i * m + k], 0, m, rl);
+    } else {
+      for (int i = k + 1 + rw; i < m; i += 4 * rnw) {
+        double sv[4];
+        int j1[4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int ir = i + r * rnw;
-        sv[r] = ir < m ? L[(int64_t)ir * m + k] : 0.0;
-        j1[r] = m;
+        for (int r = 0; r < 4; ++r) {
+          const int ir = i + r * rnw;
+          sv[r] = ir < m ? L[(int64_t)ir * m + k] : 0.0;
+          j1[r] = m;
+        }
+        rows4_axpy(A, m, i, rnw, m, sv, j1, col, 0, rl);
       }
-      rows4_axpy(A, m, i, rnw, m, sv, j1, col, 0, rl);
     }
     __syncthreads();
   }
@@ -1290,16 +1322,20 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
       vtmp[i] = L[(int64_t)i * m + k];            // column k of L, read once
     }
     __syncthreads();
-    for (int i = rw; i < m; i += 4 * rnw) {
-      double sv[4];
-      int j1[4];
+    if (m <= kRows4Min) {
+      for (int i = rw; i < m; i += rnw) row_axpy(A + (int64_t)i * m, vtmp, col[i], k + 1, m, rl);
+    } else {
+      for (int i = rw; i < m; i += 4 * rnw) {
+        double sv[4];
+        int j1[4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int ir = i + r * rnw;
-        sv[r] = ir < m ? col[ir] : 0.0;
-        j1[r] = m;
+        for (int r = 0; r < 4; ++r) {
+          const int ir = i + r * rnw;
+          sv[r] = ir < m ? col[ir] : 0.0;
+          j1[r] = m;
+        }
+        rows4_axpy(A, m, i, rnw, m, sv, j1, vtmp, k + 1, rl);
       }
-      rows4_axpy(A, m, i, rnw, m, sv, j1, vtmp, k + 1, rl);
     }
     __syncthreads();
   }
@@ -1358,20 +1394,32 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
         vtmp[j] = beta * sum;
       }
       __syncthreads();
-      for (int i = k + 1 + rw; i < m; i += 4 * rnw) {
-        double sv[4];
-        int j1[4];
+      if (m <= kRows4Min) {
+        for (int i = k + 1 + rw; i < m; i += rnw) row_axpy(A + (int64_t)i * m, vtmp, col[i], k, m, rl);
+      } else {
+        for (int i = k + 1 + rw; i < m; i += 4 * rnw) {
+          double sv[4];
+          int j1[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const int ir = i + r * rnw;
-          sv[r] = ir < m ? col[ir] : 0.0;
-          j1[r] = m;
+          for (int r = 0; r < 4; ++r) {
+            const int ir = i + r * rnw;
+            sv[r] = ir < m ? col[ir] : 0.0;
+            j1[r] = m;
+          }
+          rows4_axpy(A, m, i, rnw, m, sv, j1, vtmp, k, rl);
         }
-        rows4_axpy(A, m, i, rnw, m, sv, j1, vtmp, k, rl);
       }
       __syncthreads();
       // right: all rows, columns k+1.. (warp per row)
-      for (int i = rw; i < m; i += 4 * rnw) rows4_dot_axpy(A, m, i, rnw, m, col, beta, k + 1, m, rl);
+      if (m <= kRows4Min) {
+        for (int i = rw; i < m; i += rnw) {
+          double zi = row_dot(A + (int64_t)i * m, col, k + 1, m, rl);
+          for (int o = 16; o > 0; o >>= 1) zi += __shfl_xor_sync(0xffffffffu, zi, o);
+          row_axpy(A + (int64_t)i * m, col, zi * beta, k + 1, m, rl);
+        }
+      } else {
+        for (int i = rw; i < m; i += 4 * rnw) rows4_dot_axpy(A, m, i, rnw, m, col, beta, k + 1, m, rl);
+      }
       __syncthreads();
     }
     // store the reflector below the subdiagonal
