@@ -1342,8 +1342,11 @@ cudaError_t launch_tc_prepared(const uint8_t* opA, const uint8_t* opBS, const ui
   P.ld = 0;
   P.tiles = tiles;
   P.ntiles = ntiles;
-  int64_t range = 8192;
-  while (range > kTmaStageK && ((ns + range - 1) / range) * ntiles < 8LL * sms) range /= 2;
+  // sample ranges of up to 16384 (512 stages): each unit ends in one flush of its sums with
+  // FP64 atomics and one wait for its first interval's drain, so units are kept long; at
+  // least four units per SM keep the tail short
+  int64_t range = 16384;
+  while (range > kTmaStageK && ((ns + range - 1) / range) * ntiles < 4LL * sms) range /= 2;
   P.range_len = range;
   P.nunits = ((ns + range - 1) / range) * ntiles;
   static int flush = -1;
