@@ -118,7 +118,6 @@ struct blm_handle {
   DirBlock* d_dirb = nullptr;
   TcTile* d_tc1 = nullptr;  int ntc1 = 0;   // pass-1 tensor-core tiles
   TcTile* d_tc2 = nullptr;  int ntc2 = 0;   // combined tensor-core tiles
-  int tc1_aligned = 0, tc2_aligned = 0;     // tile parameter offsets all multiples of 4
   int off_aligned = 0;                     // block offsets all multiples of 4
   // host staging
   void* d_stage[2][4] = {{nullptr}};
@@ -506,7 +505,7 @@ blm_status accumulate_dev(blm_handle* h, const T* O, const T* G, const T* E, con
     Prof pr(h, PC_TC1);
     cudaError_t e = launch_tc_accumulate((const float*)O, (const float*)G, (const float*)E,
                                          (const float*)w, ns, h->n, ld, h->d_shift32, h->d_tc1,
-                                         h->ntc1, h->tc1_aligned, h->d_status + h->nb + 2,
+                                         h->ntc1, h->d_status + h->nb + 2,
                                          h->prec == BLM_PREC_TF32X3, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "launch_tc_accumulate");
   }
@@ -569,7 +568,7 @@ blm_status project_dev(blm_handle* h, const T* O, const T* G, const T* E, const 
       } else {
         Prof pr(h, PC_TC2);
         cudaError_t e = launch_tc_accumulate(PY, PZ, Es, ws, cnt, dc, dc, nullptr, h->d_tc2,
-                                             h->ntc2, h->tc2_aligned, h->d_status + h->nb + 2,
+                                             h->ntc2, h->d_status + h->nb + 2,
                                              h->prec == BLM_PREC_TF32X3, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "launch_tc_accumulate (combined)");
       }
@@ -814,15 +813,6 @@ blm_status blm_create(const blm_problem* p, void* stream, blm_handle** out) {
              t2.end());
     h->ntc1 = (int)t1.size();
     h->ntc2 = (int)t2.size();
-    auto aligned = [](const std::vector<TcTile>& v) {
-      for (const TcTile& t : v) {
-        const int64_t pb = t.col0 >= t.m ? t.col0 - t.m : t.col0;
-        if ((t.lo + t.row0) % 4 != 0 || (t.lo + pb) % 4 != 0) return 0;
-      }
-      return 1;
-    };
-    h->tc1_aligned = aligned(t1);
-    h->tc2_aligned = aligned(t2);
     s = upload(h, t1, &h->d_tc1);
     if (s == BLM_OK) s = upload(h, t2, &h->d_tc2);
   }

@@ -112,12 +112,12 @@ cudaError_t launch_tc_prepared(const uint8_t* opA, const uint8_t* opBS, const ui
                                int64_t nrows, int64_t row_bytes, int64_t ns, const TcTile* tiles,
                                int ntiles, int weighted, int32_t* err, cudaStream_t st);
 bool tc_supported();
-// Tensor-core contraction of one chunk (blm_sweep_tc.cu).  tiles_aligned: every tile's parameter
-// offsets are multiples of 4 (TMA staging allowed).
+// Tensor-core contraction of one chunk from FP32 rows converted in the kernel (blm_sweep_tc.cu,
+// tc_accumulate_kernel; the TF32X3 path).
 cudaError_t launch_tc_accumulate(const float* Y, const float* Z, const float* E, const float* w,
                                  int64_t ns, int64_t ncols, int64_t ld, const float* shift32,
-                                 const TcTile* tiles, int ntiles, int tiles_aligned, int32_t* err,
-                                 int tf32, cudaStream_t st);
+                                 const TcTile* tiles, int ntiles, int32_t* err, int tf32,
+                                 cudaStream_t st);
 
 // ------------------------------- launchers (blm_assemble.cu) ---------------------------------
 struct BlockAsm {

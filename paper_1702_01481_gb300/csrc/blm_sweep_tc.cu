@@ -62,8 +62,6 @@ enum { A_VIEW = 0, A_FROM_B = 1, A_SEPARATE = 2 };
 struct Bars {
   uint64_t op_full[4];       // operand ring (kStages slots, four in tc_op_kernel)
   uint64_t op_empty[4];
-  uint64_t f_full[3];        // TMA-staged kernel: FP32 tile ring
-  uint64_t f_empty[3];
   uint64_t l1_full;
   uint64_t l1_empty;
   uint64_t db_full[2];       // prepared-operand kernel: double-buffered accumulator
@@ -659,28 +657,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_accumulate_kernel(const Params
   }
 }
 
-// ---------------------------------------------------------------------------------------------
-// TMA-staged variant for BF16X4 (tiles whose parameter offsets are multiples of 4 floats, rows
-// 16-byte aligned).  Warp 1 streams FP32 sample tiles -- 16 samples x 256 parameters of Y and,
-// for X tiles, of Z; 16 x 128 for A rows outside B -- into a three-deep shared-memory ring with
-// cp.async.bulk.tensor (one thread, no register staging); ten converter warps turn two such
-// tiles into one 32-sample operand stage.  An operand row of 128 bytes holds one parameter's
-// [hi(32 samples) | lo(32 samples)], so the MMA reads hi at K offsets 0 and 32 bytes and lo at
-// 64 and 96 bytes of the same 128-byte-swizzled row: the four products of two K steps per
-// stage.  Epilogue and accumulator intervals as in tc_accumulate_kernel.
-// ---------------------------------------------------------------------------------------------
-constexpr int kTmaSub = 16;                              // samples per FP32 tile
-constexpr int kTmaStageK = 32;                           // samples per operand stage
-constexpr int kFStages = 3;
-constexpr int kFBoxB = kTmaSub * kBRows * 4;             // 16 KB
-constexpr int kFBoxA = kTmaSub * kARows * 4;             // 8 KB
-constexpr int kFStageBytes = 2 * kFBoxB + kFBoxA;        // Y, Z, separate A rows: 40 KB
-constexpr int kOpStageBytes = (kBRows + kARows) * 128;   // 48 KB
-constexpr int kTmaFOffset = kStages * kOpStageBytes;     // 96 KB
-constexpr int kTmaBarOffset = kTmaFOffset + kFStages * kFStageBytes;   // 216 KB
-constexpr int kTmaSmemBytes = kTmaBarOffset + 256 + 1024;
-constexpr int kConvWarpsT = 10;
-static_assert(kTmaSmemBytes <= 227 * 1024, "TMA-staged kernel exceeds shared memory");
+// Samples per operand stage of the TMA-fed kernel (two K steps of 16 per 128-byte row half).
+constexpr int kTmaStageK = 32;
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
@@ -695,261 +673,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       "%3}], [%4];" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
-}
-
-__device__ __forceinline__ float lds_f1(uint32_t addr) {
-  float v;
-  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
-  return v;
-}
-
-// Converter job: 32 operand rows x 8 samples (sample group sg of the 32-sample stage, taken
-// from FP32 tile sg / 2).  Lane l owns row 32 rowgroup + l: its shared-memory reads of one sample
-// are 32 consecutive floats (one wavefront) and its two 16-byte stores (hi and lo of 8 samples)
-// fall in 8 different rows per quarter warp, so both are conflict-free.  kind 0: B rows (Y' or
-// X', weighted; A rows too in A_FROM_B mode); kind 1: separate A rows (Y').
-__device__ __forceinline__ void convert_job_tma(const Params& P, const TileInfo& ti, int kind,
-                                                int rowgroup, int sg, int64_t stage_base,
-                                                int64_t s_end, uint32_t ftile, uint32_t op,
-                                                float sh, float e_reg, float w_reg) {
-  const int lane = threadIdx.x & 31;
-  const bool xt = (kind == 0) && ti.xtype;
-  const int r0 = (sg & 1) * 8;                   // first row of these samples in the tile
-  const int row = rowgroup * 32 + lane;
-  const bool vr = row < (kind == 0 ? ti.nB : ti.nA);
-  const int rowlen = kind == 0 ? kBRows : kARows;
-  const uint32_t ysrc = ftile + (kind == 0 ? 0u : (uint32_t)(2 * kFBoxB)) + (uint32_t)(row * 4);
-  const uint32_t zsrc = ftile + (uint32_t)kFBoxB + (uint32_t)(row * 4);
-  float y[8], z[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    y[q] = lds_f1(ysrc + (uint32_t)((r0 + q) * rowlen * 4));
-    z[q] = xt ? lds_f1(zsrc + (uint32_t)((r0 + q) * kBRows * 4)) : 0.0f;
-  }
-  float yy[8], x[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int64_t s = stage_base + 8 * sg + q;
-    const bool ok = vr && s < s_end;
-    // E and w of the tile's 16 samples sit in lanes 0..15 (loaded once per tile)
-    const float e_s = __shfl_sync(0xffffffffu, e_reg, r0 + q);
-    const float w_s = __shfl_sync(0xffffffffu, w_reg, r0 + q);
-    const float e = (xt && ok) ? e_s : 0.0f;
-    const float wv = (kind == 0 && P.w && ok) ? w_s : 1.0f;
-    yy[q] = ok ? y[q] - sh : 0.0f;
-    x[q] = (xt ? fmaf(e, yy[q], z[q]) : yy[q]) * wv;
-  }
-  uint4 hi, lo;
-  if (kind == 0) {
-    split8(x, hi, lo);
-    st_shared_v4(op + swz(row, sg), hi);
-    st_shared_v4(op + swz(row, 4 + sg), lo);
-    const int arow = ti.pb + row - ti.row0;
-    if (ti.amode == A_FROM_B && arow >= 0 && arow < kARows) {
-      split8(yy, hi, lo);
-      st_shared_v4(op + kBRows * 128 + swz(arow, sg), hi);
-      st_shared_v4(op + kBRows * 128 + swz(arow, 4 + sg), lo);
-    }
-  } else {
-    split8(yy, hi, lo);
-    st_shared_v4(op + kBRows * 128 + swz(row, sg), hi);
-    st_shared_v4(op + kBRows * 128 + swz(row, 4 + sg), lo);
-  }
-}
-
-__global__ void __launch_bounds__(kThreads, 1)
-tc_tma_kernel(const Params P, const __grid_constant__ CUtensorMap mapY,
-              const __grid_constant__ CUtensorMap mapZ, const __grid_constant__ CUtensorMap mapA) {
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  Bars* bars = (Bars*)(smem + kTmaBarOffset);
-  const int warp = threadIdx.x >> 5;
-  const int lane = threadIdx.x & 31;
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&bars->op_full[s], kConvWarpsT);
-      mbar_init(&bars->op_empty[s], 1);
-    }
-    for (int s = 0; s < kFStages; ++s) {
-      mbar_init(&bars->f_full[s], 1);
-      mbar_init(&bars->f_empty[s], kConvWarpsT);
-    }
-    mbar_init(&bars->l1_full, 1);
-    mbar_init(&bars->l1_empty, 4);
-    mbar_init(&bars->drain, 1);
-    bars->abort = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
-                     smem_u32(&bars->tmem_base))
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = bars->tmem_base;
-  const int fs = P.flush_stages;
-  const uint32_t fbase = smem_u32(smem + kTmaFOffset);
-
-  if (warp == 0) {
-    // ------------------------------- MMA issuer -------------------------------
-    uint32_t g = 0, k = 0;
-    bool alive = true;
-    for (int64_t u = blockIdx.x; u < P.nunits && alive; u += gridDim.x) {
-      const TileInfo ti = decode_tile(P.tiles[u % P.ntiles], P.w != nullptr);
-      const int64_t sa = (u / P.ntiles) * P.range_len;
-      const int64_t sb = min(P.ns, sa + P.range_len);
-      const int nst = (int)((sb - sa + kTmaStageK - 1) / kTmaStageK);
-      for (int st = 0; st < nst && alive; ++st, ++g) {
-        const uint32_t slot = g % kStages, use = g / kStages;
-        uint32_t acc = 1;
-        const bool istart = (st == 0) || ((st - 1) % fs == 0);
-        const bool iend = (st == 0) || ((st - 1) % fs == fs - 1) || (st == nst - 1);
-        if (istart) {
-          alive = mbar_wait(&bars->l1_empty, (k & 1) ^ 1, bars, P.err, 11);
-          tc_fence_after();
-          acc = (st == 0) ? 0 : 1;
-        }
-        if (alive) alive = mbar_wait(&bars->op_full[slot], use & 1, bars, P.err, 12);
-        if (!alive) break;
-        tc_fence_after();
-        if (lane == 0) {
-          const uint32_t ob = smem_u32(smem + slot * kOpStageBytes);
-          const uint32_t oa = (ti.amode == A_VIEW) ? ob + (uint32_t)(ti.row0 - ti.pb) * 128u
-                                                   : ob + (uint32_t)kBRows * 128u;
-#pragma unroll
-          for (int ks = 0; ks < 2; ++ks) {
-            const uint32_t o = ks * 32;
-            mma_bf16(tmem, sdesc(oa + o), sdesc(ob + o), acc);        // hi * hi
-            mma_bf16(tmem, sdesc(oa + o), sdesc(ob + 64 + o), 1);     // hi * lo
-            mma_bf16(tmem, sdesc(oa + 64 + o), sdesc(ob + o), 1);     // lo * hi
-            mma_bf16(tmem, sdesc(oa + 64 + o), sdesc(ob + 64 + o), 1);  // lo * lo
-            acc = 1;
-          }
-          mma_commit(&bars->op_empty[slot]);
-          if (iend) mma_commit(&bars->l1_full);
-        }
-        __syncwarp();
-        if (iend) ++k;
-      }
-    }
-    if (lane == 0) mma_commit(&bars->drain);
-    __syncwarp();
-    for (uint32_t i = 0; i < kWaitLimit && !mbar_try_wait(&bars->drain, 0); ++i) {
-    }
-  } else if (warp == 1) {
-    // ------------------------------- TMA producer ------------------------------
-    uint32_t f = 0;
-    uint32_t armed[kFStages] = {0, 0, 0};
-    bool alive = true;
-    for (int64_t u = blockIdx.x; u < P.nunits && alive; u += gridDim.x) {
-      const TileInfo ti = decode_tile(P.tiles[u % P.ntiles], P.w != nullptr);
-      const int64_t sa = (u / P.ntiles) * P.range_len;
-      const int64_t sb = min(P.ns, sa + P.range_len);
-      const int nsub = 2 * (int)((sb - sa + kTmaStageK - 1) / kTmaStageK);
-      const uint32_t bytes = (uint32_t)kFBoxB * (ti.xtype ? 2u : 1u) +
-                             (ti.amode == A_SEPARATE ? (uint32_t)kFBoxA : 0u);
-      for (int h = 0; h < nsub && alive; ++h, ++f) {
-        const uint32_t slot = f % kFStages, use = f / kFStages;
-        alive = mbar_wait(&bars->f_empty[slot], (use & 1) ^ 1, bars, P.err, 15);
-        if (!alive) break;
-        if (lane == 0) {
-          uint64_t* bar = &bars->f_full[slot];
-          const uint32_t dst = fbase + slot * (uint32_t)kFStageBytes;
-          const int ys = (int)(sa + (int64_t)h * kTmaSub);
-          mbar_expect_tx(bar, bytes);
-          tma_load_2d(dst, &mapY, (int)(ti.lo + ti.pb), ys, bar);
-          if (ti.xtype) tma_load_2d(dst + kFBoxB, &mapZ, (int)(ti.lo + ti.pb), ys, bar);
-          if (ti.amode == A_SEPARATE)
-            tma_load_2d(dst + 2 * kFBoxB, &mapA, (int)(ti.lo + ti.row0), ys, bar);
-        }
-        __syncwarp();
-        armed[slot] = use + 1;
-      }
-    }
-    // every armed tile must have landed before the CTA can exit
-    for (int s = 0; s < kFStages; ++s)
-      if (armed[s] > 0) {
-        for (uint32_t i = 0; i < kWaitLimit && !mbar_try_wait(&bars->f_full[s], (armed[s] - 1) & 1);
-             ++i) {
-        }
-      }
-  } else if (warp >= 4 && warp < 8) {
-    epilogue_role<kTmaStageK, 4>(P, bars, tmem, warp, lane, fs);
-  } else {
-    // ------------------------------- converters -------------------------------
-    const int cw = warp < 4 ? warp - 2 : warp - 6;   // 0 .. kConvWarpsT - 1
-    uint32_t g = 0, f = 0;
-    bool alive = true;
-    for (int64_t u = blockIdx.x; u < P.nunits && alive; u += gridDim.x) {
-      const TileInfo ti = decode_tile(P.tiles[u % P.ntiles], P.w != nullptr);
-      const int64_t sa = (u / P.ntiles) * P.range_len;
-      const int64_t sb = min(P.ns, sa + P.range_len);
-      const int nst = (int)((sb - sa + kTmaStageK - 1) / kTmaStageK);
-      // jobs of one FP32 tile: (row group, sample group) over B rows, then separate A rows
-      const int nb_rg = kBRows / 32, na_rg = (ti.amode == A_SEPARATE) ? kARows / 32 : 0;
-      const int njobs = 2 * (nb_rg + na_rg);
-      // this warp's jobs j = cw + 10 i keep their rows for the whole unit: load their shifts once
-      float shv[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const int j = cw + kConvWarpsT * i;
-        shv[i] = 0.0f;
-        if (j < njobs && P.shift) {
-          const int jr = j >> 1;
-          const int kind = jr < nb_rg ? 0 : 1;
-          const int row = (kind ? jr - nb_rg : jr) * 32 + lane;
-          if (row < (kind ? ti.nA : ti.nB))
-            shv[i] = __ldg(P.shift + ti.lo + (kind ? ti.row0 : ti.pb) + row);
-        }
-      }
-      for (int st = 0; st < nst; ++st, ++g) {
-        const uint32_t slot = g % kStages, use = g / kStages;
-        alive = mbar_wait(&bars->op_empty[slot], (use & 1) ^ 1, bars, P.err, 14);
-        if (!alive) break;
-        const uint32_t op = smem_u32(smem + slot * kOpStageBytes);
-        const int64_t base = sa + (int64_t)st * kTmaStageK;
-        // each 16-sample tile is released as soon as every warp is done with it
-        for (int half = 0; half < 2 && alive; ++half, ++f) {
-          const uint32_t fslot = f % kFStages;
-          // E and w of this tile's samples (lanes 0..15), issued before the wait on the tile
-          const int64_t ys = base + 16 * half + (lane & 15);
-          const float e_reg = (ti.xtype && ys < sb) ? __ldg(P.E + ys) : 0.0f;
-          const float w_reg = (P.w && ys < sb) ? __ldg(P.w + ys) : 1.0f;
-          alive = mbar_wait(&bars->f_full[fslot], (f / kFStages) & 1, bars, P.err, 16);
-          if (!alive) break;
-          const uint32_t ftile = fbase + fslot * (uint32_t)kFStageBytes;
-#pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            const int j = cw + kConvWarpsT * i;
-            if (j >= njobs) break;
-            const int sg = 2 * half + (j & 1);
-            const int jr = j >> 1;
-            const int kind = jr < nb_rg ? 0 : 1;
-            convert_job_tma(P, ti, kind, kind ? jr - nb_rg : jr, sg, base, sb, ftile, op, shv[i],
-                            e_reg, w_reg);
-          }
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&bars->f_empty[fslot]);
-        }
-        if (!alive) break;
-        fence_async_smem();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&bars->op_full[slot]);
-      }
-    }
-  }
-
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem)
-                 : "memory");
-  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1218,28 +941,14 @@ EncodeTiledFn encode_tiled_fn() {
   return fn;
 }
 
-// 2-D tensor map over an ns x ncols FP32 sample array with row stride ld (elements).
-bool encode_map(CUtensorMap* m, const float* base, int64_t ncols, int64_t nrows, int64_t ld,
-                int box_x, int box_y) {
-  EncodeTiledFn fn = encode_tiled_fn();
-  if (!fn) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)ncols, (cuuint64_t)nrows};
-  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
-  cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y};
-  cuuint32_t estr[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box,
-            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
 }  // namespace
 
 cudaError_t launch_tc_accumulate(const float* Y, const float* Z, const float* E, const float* w,
                                  int64_t ns, int64_t ncols, int64_t ld, const float* shift32,
-                                 const TcTile* tiles, int ntiles, int tiles_aligned, int32_t* err,
-                                 int tf32, cudaStream_t st) {
+                                 const TcTile* tiles, int ntiles, int32_t* err, int tf32,
+                                 cudaStream_t st) {
   if (ns <= 0 || ntiles <= 0) return cudaSuccess;
   static int sms = 0;
-  static int tma_env = 1;
   if (sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1248,19 +957,7 @@ cudaError_t launch_tc_accumulate(const float* Y, const float* Z, const float* E,
                          kSmemBytes);
     cudaFuncSetAttribute(tc_accumulate_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          kSmemBytes);
-    cudaFuncSetAttribute(tc_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kTmaSmemBytes);
-    const char* env = getenv("BLM_TC_TMA");   // 0: register-staged kernel only (comparisons)
-    tma_env = env ? atoi(env) : 1;
   }
-  // TMA staging needs 16-byte aligned rows and parameter offsets and full-width boxes
-  CUtensorMap mY, mZ, mA;
-  bool tma = !tf32 && tma_env && tiles_aligned && (ld % 4 == 0) &&
-             (((uintptr_t)Y | (uintptr_t)Z) % 16 == 0) && ns >= kTmaSub && ncols >= kBRows;
-  if (tma)
-    tma = encode_map(&mY, Y, ncols, ns, ld, kBRows, kTmaSub) &&
-          encode_map(&mZ, Z, ncols, ns, ld, kBRows, kTmaSub) &&
-          encode_map(&mA, Y, ncols, ns, ld, kARows, kTmaSub);
   Params P;
   P.Y = Y;
   P.Z = Z;
@@ -1273,7 +970,7 @@ cudaError_t launch_tc_accumulate(const float* Y, const float* Z, const float* E,
   P.ntiles = ntiles;
   // sample ranges: enough units to keep every SM busy with a small tail
   int64_t range = 8192;
-  const int64_t sk = tma ? kTmaStageK : (tf32 ? kStageKTf : kStageK);
+  const int64_t sk = tf32 ? kStageKTf : kStageK;
   while (range > sk && ((ns + range - 1) / range) * ntiles < 8LL * sms) range /= 2;
   P.range_len = range;
   P.nunits = ((ns + range - 1) / range) * ntiles;
@@ -1288,9 +985,7 @@ cudaError_t launch_tc_accumulate(const float* Y, const float* Z, const float* E,
   P.err = err;
   P.vec_ok = (ld % 4 == 0) && (((uintptr_t)Y | (uintptr_t)Z) % 16 == 0);
   const int grid = (int)(P.nunits < sms ? P.nunits : sms);
-  if (tma)
-    tc_tma_kernel<<<grid, kThreads, kTmaSmemBytes, st>>>(P, mY, mZ, mA);
-  else if (tf32)
+  if (tf32)
     tc_accumulate_kernel<true><<<grid, kThreads, kSmemBytes, st>>>(P);
   else
     tc_accumulate_kernel<false><<<grid, kThreads, kSmemBytes, st>>>(P);

@@ -125,7 +125,7 @@ def test_block_larger_than_tile(torch_cuda):
 
 def test_combined_sums_of_256_directions(torch_cuda):
     """16 blocks of 32 with K = 16: the combined problem has 256 directions, so the second sweep's
-    contraction runs with full-width (TMA-staged) tiles as in the 16384-parameter step."""
+    contraction runs with full-width tiles as in the 16384-parameter step."""
     wl = synth.Workload("t", 512, 4096, synth.equal_blocks(512, 16), 16, decades=4.0, chunk=4096,
                         seed=8)
     O, G, E = f32_inputs(wl)
