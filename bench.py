@@ -358,18 +358,22 @@ def run_e2e(args):
 
     one_step()
     torch.cuda.synchronize()
-    t = time.perf_counter()
-    steps = max(1, args.e2e_steps)
-    for _ in range(steps):
+    # each step timed on its own (host clock around a synchronised step); the median is reported,
+    # since a step of the host-to-device stream can be disturbed by the host
+    times = []
+    for _ in range(max(1, args.e2e_steps)):
+        t = time.perf_counter()
         one_step()
-    torch.cuda.synchronize()
-    sec = (time.perf_counter() - t) / steps
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t)
+    sec = sorted(times)[len(times) // 2]
     step.close()
     flop = useful_flop_per_sample(wl) * ns
     h2d = 2 * 2 * ns * n * O.element_size() + 2 * ns * E.element_size()
     return {"value": round(flop / sec / 1e9, 1), "unit": "sample-GFLOP/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 * n + 8,
-            "samples_per_step": ns, "ms_per_step": round(sec * 1e3, 1)}
+            "samples_per_step": ns, "ms_per_step": round(sec * 1e3, 1),
+            "ms_per_step_all": [round(x * 1e3, 1) for x in times]}
 
 
 def cpu_baseline(args, wl, samples):
@@ -400,7 +404,7 @@ def main():
     ap.add_argument("--samples", type=int, default=0)
     ap.add_argument("--cpu-samples", type=int, default=2048)
     ap.add_argument("--e2e-samples", type=int, default=131072)
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
