@@ -428,18 +428,13 @@ __device__ __forceinline__ float preload_coef(int i, int nst, int fs) {
   return -0.5f * (float)interval_len(i, nst, fs) / (float)(1 + (i - 1) * fs);
 }
 
-// Epilogue role (NW = 4 warps 4-7, one per 32-lane tensor-memory quadrant, or NW = 8 warps
-// 4-11, two per quadrant each taking 128 of the 256 columns): at the end of each accumulator
-// interval add L1 into L2 (or, at the end of a unit, L2 + L1 into the FP64 sums) and preload L1.
-// The MMA warp waits for this drain before the next interval, so it is kept short: with eight
-// warps columns move in pairs of 32-column chunks (four tensor-memory loads per wait).
-template <int SK, int NW>
+// Epilogue role of tc_accumulate_kernel (warps 4-7, one per 32-lane tensor-memory quadrant): at
+// the end of each accumulator interval add L1 into L2 (or, at the end of a unit, L2 + L1 into the
+// FP64 sums) and preload L1 for the next interval.
+template <int SK>
 __device__ __forceinline__ void epilogue_role(const Params& P, Bars* bars, uint32_t tmem, int warp,
                                               int lane, int fs) {
-  static_assert(NW == 4 || NW == 8, "four or eight epilogue warps");
-  constexpr int kSpan = 256 * 4 / NW;              // columns per warp
   const int q = warp & 3;                          // tensor-memory lane quadrant
-  const int cbase = ((warp >> 2) - 1) * kSpan;     // warps 4-7: 0; warps 8-11: 128
   const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
   uint32_t k = 0;
   bool alive = true;
@@ -458,7 +453,11 @@ __device__ __forceinline__ void epilogue_role(const Params& P, Bars* bars, uint3
       const float c_next = last ? 0.0f : preload_coef(it + 1, nst, fs);
       const int row = 32 * q + lane;
       const bool vrow = row < ti.nA;
-      auto chunk = [&](uint32_t* a, uint32_t* b, int cc) {
+      for (int cc = 0; cc < 256; cc += 32) {
+        uint32_t a[32], b[32];
+        TMEM_LD32(lane_addr + cc, a);
+        if (!first) TMEM_LD32(lane_addr + 256 + cc, b);
+        tmem_wait_ld();
         if (last) {
           if (vrow) {
             double* orow = ti.out + (int64_t)(ti.row0 + row) * 2 * ti.m + ti.col0 + cc;
@@ -483,28 +482,6 @@ __device__ __forceinline__ void epilogue_role(const Params& P, Bars* bars, uint3
           }
           TMEM_ST32(lane_addr + 256 + cc, b);
           TMEM_ST32(lane_addr + cc, a);
-        }
-      };
-      if (NW == 8) {
-        for (int cc = cbase; cc < cbase + kSpan; cc += 64) {
-          uint32_t a0[32], b0[32], a1[32], b1[32];
-          TMEM_LD32(lane_addr + cc, a0);
-          TMEM_LD32(lane_addr + cc + 32, a1);
-          if (!first) {
-            TMEM_LD32(lane_addr + 256 + cc, b0);
-            TMEM_LD32(lane_addr + 256 + cc + 32, b1);
-          }
-          tmem_wait_ld();
-          chunk(a0, b0, cc);
-          chunk(a1, b1, cc + 32);
-        }
-      } else {
-        for (int cc = cbase; cc < cbase + kSpan; cc += 32) {
-          uint32_t a0[32], b0[32];
-          TMEM_LD32(lane_addr + cc, a0);
-          if (!first) TMEM_LD32(lane_addr + 256 + cc, b0);
-          tmem_wait_ld();
-          chunk(a0, b0, cc);
         }
       }
       tmem_wait_st();
@@ -609,7 +586,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_accumulate_kernel(const Params
     for (uint32_t i = 0; i < kWaitLimit && !mbar_try_wait(&bars->drain, 0); ++i) {
     }
   } else if (warp >= 4 && warp < 8) {
-    epilogue_role<stage_k<TF>(), 4>(P, bars, tmem, warp, lane, fs);
+    epilogue_role<stage_k<TF>()>(P, bars, tmem, warp, lane, fs);
   } else {
     // ------------------------------- converters -------------------------------
     const int cw = warp < 4 ? warp - 1 : warp - 5;   // 0 .. kConvWarps-1
