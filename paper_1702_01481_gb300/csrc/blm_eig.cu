@@ -1243,101 +1243,105 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
     return;
   }
   EIG_MARK(1);
-  // ---- 2a. Cholesky (right-looking, lower) ----
-  for (int k = 0; k < m; ++k) {
-    if (t == 0) {
-      const double p = L[(int64_t)k * m + k];
-      if (!(p > 1e-15)) {
-        sh.iscal[1] = ST_NOT_PD;
+  // The Davidson projection's overlap is the identity (S-orthonormal basis): L = I and A = H
+  // as assembled above, so the Cholesky factorisation and the reduction are skipped.
+  if (!pb.fp32_locate) {
+    // ---- 2a. Cholesky (right-looking, lower) ----
+    for (int k = 0; k < m; ++k) {
+      if (t == 0) {
+        const double p = L[(int64_t)k * m + k];
+        if (!(p > 1e-15)) {
+          sh.iscal[1] = ST_NOT_PD;
+        } else {
+          L[(int64_t)k * m + k] = sqrt(p);
+          sh.scal[0] = 1.0 / sqrt(p);
+        }
+      }
+      __syncthreads();
+      if (sh.iscal[1] != ST_OK) break;
+      const double inv = sh.scal[0];
+      for (int i = k + 1 + t; i < m; i += nt) {
+        const double v = L[(int64_t)i * m + k] * inv;
+        L[(int64_t)i * m + k] = v;
+        col[i] = v;
+      }
+      __syncthreads();
+      if (m <= kRows4Min) {
+        for (int i = k + 1 + rw; i < m; i += rnw)
+          row_axpy(L + (int64_t)i * m, col, col[i], k + 1, i + 1, rl);
       } else {
-        L[(int64_t)k * m + k] = sqrt(p);
-        sh.scal[0] = 1.0 / sqrt(p);
-      }
-    }
-    __syncthreads();
-    if (sh.iscal[1] != ST_OK) break;
-    const double inv = sh.scal[0];
-    for (int i = k + 1 + t; i < m; i += nt) {
-      const double v = L[(int64_t)i * m + k] * inv;
-      L[(int64_t)i * m + k] = v;
-      col[i] = v;
-    }
-    __syncthreads();
-    if (m <= kRows4Min) {
-      for (int i = k + 1 + rw; i < m; i += rnw)
-        row_axpy(L + (int64_t)i * m, col, col[i], k + 1, i + 1, rl);
-    } else {
-      for (int i = k + 1 + rw; i < m; i += 4 * rnw) {
-        double sv[4];
-        int j1[4];
+        for (int i = k + 1 + rw; i < m; i += 4 * rnw) {
+          double sv[4];
+          int j1[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const int ir = i + r * rnw;
-          sv[r] = ir < m ? col[ir] : 0.0;
-          j1[r] = ir + 1;
+          for (int r = 0; r < 4; ++r) {
+            const int ir = i + r * rnw;
+            sv[r] = ir < m ? col[ir] : 0.0;
+            j1[r] = ir + 1;
+          }
+          rows4_axpy(L, m, i, rnw, m, sv, j1, col, k + 1, rl);
         }
-        rows4_axpy(L, m, i, rnw, m, sv, j1, col, k + 1, rl);
       }
+      __syncthreads();
     }
-    __syncthreads();
-  }
-  if (sh.iscal[1] != ST_OK) {
-    if (t == 0) *pb.status = sh.iscal[1];
-    return;
-  }
-  // ---- 2b. A <- L^-1 A (row forward substitution) ----
-  for (int k = 0; k < m; ++k) {
-    const double inv = 1.0 / L[(int64_t)k * m + k];
-    for (int j = t; j < m; j += nt) {
-      const double v = A[(int64_t)k * m + j] * inv;
-      A[(int64_t)k * m + j] = v;
-      col[j] = v;
+    if (sh.iscal[1] != ST_OK) {
+      if (t == 0) *pb.status = sh.iscal[1];
+      return;
     }
-    __syncthreads();
-    if (m <= kRows4Min) {
-      for (int i = k + 1 + rw; i < m; i += rnw)
-        row_axpy(A + (int64_t)i * m, col, L[(int64_t)i * m + k], 0, m, rl);
-    } else {
-      for (int i = k + 1 + rw; i < m; i += 4 * rnw) {
-        double sv[4];
-        int j1[4];
+    // ---- 2b. A <- L^-1 A (row forward substitution) ----
+    for (int k = 0; k < m; ++k) {
+      const double inv = 1.0 / L[(int64_t)k * m + k];
+      for (int j = t; j < m; j += nt) {
+        const double v = A[(int64_t)k * m + j] * inv;
+        A[(int64_t)k * m + j] = v;
+        col[j] = v;
+      }
+      __syncthreads();
+      if (m <= kRows4Min) {
+        for (int i = k + 1 + rw; i < m; i += rnw)
+          row_axpy(A + (int64_t)i * m, col, L[(int64_t)i * m + k], 0, m, rl);
+      } else {
+        for (int i = k + 1 + rw; i < m; i += 4 * rnw) {
+          double sv[4];
+          int j1[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const int ir = i + r * rnw;
-          sv[r] = ir < m ? L[(int64_t)ir * m + k] : 0.0;
-          j1[r] = m;
+          for (int r = 0; r < 4; ++r) {
+            const int ir = i + r * rnw;
+            sv[r] = ir < m ? L[(int64_t)ir * m + k] : 0.0;
+            j1[r] = m;
+          }
+          rows4_axpy(A, m, i, rnw, m, sv, j1, col, 0, rl);
         }
-        rows4_axpy(A, m, i, rnw, m, sv, j1, col, 0, rl);
       }
+      __syncthreads();
     }
-    __syncthreads();
-  }
-  // ---- 2c. A <- A L^-T (column forward substitution) ----
-  for (int k = 0; k < m; ++k) {
-    const double inv = 1.0 / L[(int64_t)k * m + k];
-    for (int i = t; i < m; i += nt) {
-      const double v = A[(int64_t)i * m + k] * inv;
-      A[(int64_t)i * m + k] = v;
-      col[i] = v;
-      vtmp[i] = L[(int64_t)i * m + k];            // column k of L, read once
-    }
-    __syncthreads();
-    if (m <= kRows4Min) {
-      for (int i = rw; i < m; i += rnw) row_axpy(A + (int64_t)i * m, vtmp, col[i], k + 1, m, rl);
-    } else {
-      for (int i = rw; i < m; i += 4 * rnw) {
-        double sv[4];
-        int j1[4];
+    // ---- 2c. A <- A L^-T (column forward substitution) ----
+    for (int k = 0; k < m; ++k) {
+      const double inv = 1.0 / L[(int64_t)k * m + k];
+      for (int i = t; i < m; i += nt) {
+        const double v = A[(int64_t)i * m + k] * inv;
+        A[(int64_t)i * m + k] = v;
+        col[i] = v;
+        vtmp[i] = L[(int64_t)i * m + k];            // column k of L, read once
+      }
+      __syncthreads();
+      if (m <= kRows4Min) {
+        for (int i = rw; i < m; i += rnw) row_axpy(A + (int64_t)i * m, vtmp, col[i], k + 1, m, rl);
+      } else {
+        for (int i = rw; i < m; i += 4 * rnw) {
+          double sv[4];
+          int j1[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const int ir = i + r * rnw;
-          sv[r] = ir < m ? col[ir] : 0.0;
-          j1[r] = m;
+          for (int r = 0; r < 4; ++r) {
+            const int ir = i + r * rnw;
+            sv[r] = ir < m ? col[ir] : 0.0;
+            j1[r] = m;
+          }
+          rows4_axpy(A, m, i, rnw, m, sv, j1, vtmp, k + 1, rl);
         }
-        rows4_axpy(A, m, i, rnw, m, sv, j1, vtmp, k + 1, rl);
       }
+      __syncthreads();
     }
-    __syncthreads();
   }
   EIG_MARK(2);
   // ---- 3. Householder reduction to Hessenberg form ----
