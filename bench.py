@@ -116,6 +116,19 @@ class Clocks:
 # ------------------------------------------------------------------------------------------------
 # our implementation
 # ------------------------------------------------------------------------------------------------
+def job_rate(elapsed_ms, steps, flop_per_rank, world, device="cpu"):
+    """Whole-job rate of `world` replicas: the slowest rank's time (all-reduce MAX, then a barrier)
+    and every rank's work.  Returns (ms per step, sample-GFLOP/s)."""
+    if world > 1:
+        import torch
+        t = torch.tensor([float(elapsed_ms)], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        elapsed_ms = float(t.item())
+    ms_step = elapsed_ms / steps
+    return ms_step, world * flop_per_rank / (ms_step / 1e3) / 1e9
+
+
 def run_ours(args, rank, world):
     import torch
     import synth
@@ -180,14 +193,8 @@ def run_ours(args, rank, world):
     blm.blm_profile(step.h, 0)
     clk = clocks.stop()
     elapsed_ms = start.elapsed_time(end)
-    if world > 1:
-        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-        elapsed_ms = float(t.item())
-    ms_step = elapsed_ms / args.steps
     flop = useful_flop_per_sample(wl) * ns
-    value = world * flop / (ms_step / 1e3) / 1e9
+    ms_step, value = job_rate(elapsed_ms, args.steps, flop, world, dev)
     res = dict(wl=wl, ms_step=ms_step, value=value, prof=prof, clocks=clk, e_pred=e_pred,
                flop=flop, steps=args.steps)
     step.close()
