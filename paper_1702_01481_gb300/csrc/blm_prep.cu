@@ -12,10 +12,11 @@
 // sum w Y', sum w E Y', sum w Z per parameter (and sum w, sum w E) into FP64, in FP32 runs of 64
 // samples per thread and parameter.
 //
-// A CTA takes 64 parameters x 1024 samples in tiles of 64 samples, double-buffered through
-// shared memory by cp.async; thread (p4, sb) owns parameters 4 p4 .. 4 p4 + 3 and samples
-// 8 sb .. 8 sb + 7 of a tile: 16-byte shared-memory reads along the parameters, one 16-byte
-// store per parameter for hi and one for lo.
+// A CTA takes 64 parameters x 1024 samples in tiles of 64 samples; thread (p4, sb) owns
+// parameters 4 p4 .. 4 p4 + 3 and samples 8 sb .. 8 sb + 7 of a tile and writes one 16-byte
+// store per parameter for hi and one for lo.  prep_direct_kernel (16-byte aligned rows, the
+// usual case) loads its tile straight into registers; prep_kernel (any alignment) stages it
+// through shared memory with cp.async, double-buffered.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>

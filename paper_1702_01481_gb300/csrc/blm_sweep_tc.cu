@@ -22,10 +22,15 @@
 //    order.  The preloaded value is recomputed bit for bit from L2 when the interval is flushed
 //    and subtracted exactly.
 // Work units are (sample range, tile) pairs; a persistent grid of one CTA per SM walks them.
-// Roles per CTA (16 warps): warp 0 allocates tensor memory and one lane issues the MMAs;
-// warps 4-7 are the epilogue (one per 32-lane tensor-memory quadrant); the other 11 warps
-// convert FP32 samples into the split-BF16 operands in shared memory (K-major, 128-byte
-// swizzle: each operand row holds 64 consecutive samples of one parameter).
+//
+// Two kernels.  tc_op_kernel (the BF16X4 path) streams operand rows prepared once per element
+// by blm_prep.cu with TMA and keeps two tensor-memory accumulators that alternate per interval,
+// the running sums in epilogue registers (described at the kernel).  tc_accumulate_kernel (the
+// TF32X3 path, or where operands are not prepared) converts FP32 samples in the kernel and uses
+// the L1 / L2 scheme above: warp 0 allocates tensor memory and one lane issues the MMAs; warps
+// 4-7 are the epilogue (one per 32-lane tensor-memory quadrant); the other 11 warps convert
+// FP32 samples into the split operands in shared memory (K-major, 128-byte swizzle: each operand
+// row holds 64 consecutive samples of one parameter).
 // Every wait on an mbarrier is bounded; on timeout the kernel records an error code, drains its
 // own MMAs, frees tensor memory and returns.
 #include <cuda.h>
