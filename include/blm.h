@@ -24,7 +24,8 @@
  *     copied through the handle's two staging buffers (256 MiB each, allocated on the
  *     handle's first host-memory call).  Element type per blm_problem.input_type.
  *   - All calls are asynchronous on the handle's stream; results are valid once it syncs.
- *   - The handle owns every accumulator and workspace it needs (allocated in blm_create).
+ *   - The handle owns every accumulator and workspace it needs (allocated in blm_create; the
+ *     host staging buffers on its first host-memory call).
  *   - Call order is enforced: accumulate+ -> block_solve -> project+ -> combined_solve;
  *     a call out of order returns BLM_ERR_STATE and changes nothing.
  *   - Numeric failures (non-finite sums, overlap not positive definite, no real lowest
@@ -72,7 +73,8 @@ typedef struct {
   const int64_t* block_offsets;   /* host, n_blocks+1 increasing, [0] = 0, [N_B] = N_V;
                                      block b is parameters [off[b], off[b+1]) (contiguous)   */
   int32_t n_keep;                 /* N_K: directions kept per block (min(N_K, M_b) used)     */
-  int32_t n_old;                  /* N_O: previous-update directions (Eq. 9), 0 = none       */
+  int32_t n_old;                  /* N_O: previous-update directions (Eq. 9), 0 = none; 0..16,
+                                     N_O > 0 needs precision BLM_PREC_F64 (FP64 input)       */
   const double* old_dirs;         /* host or device, n_old x n_params row-major: row j is the
                                      overall update of iteration n-j (Sec. II.B); block k's
                                      slice of row j is D_jk.  Copied at blm_create.          */
