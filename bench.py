@@ -24,6 +24,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -197,7 +199,6 @@ def run_ours(args, rank, world):
     ms_step, value = job_rate(elapsed_ms, args.steps, flop, world, dev)
     res = dict(wl=wl, ms_step=ms_step, value=value, prof=prof, clocks=clk, e_pred=e_pred,
                flop=flop, steps=args.steps)
-    step.close()
 
     # roofline of the dominant kernel (largest summed device time in the step)
     pk = peaks()
@@ -252,66 +253,122 @@ def run_ours(args, rank, world):
     res["roofline"] = roof
     res["gpu_launches"] = int(sum(v[1] for v in prof.values()))
 
-    # plain FP64 GPU path on one chunk of the same workload (FP64 samples), scaled to ns
+    # the plain FP64 GPU path over the same resident samples (FP32 values widened to FP64 on
+    # load), one full step: the denominator of the mixed path's speed-up, and the reference the
+    # mixed step states its error against (the FP64 path matches the FP64 oracle to 1e-10)
     if mixed and not args.no_fp64 and rank == 0:
-        del O, G, E
-        torch.cuda.empty_cache()
-        c = min(chunk, ns)
-        O64 = torch.empty((c, n), dtype=torch.float64, device=dev)
-        G64 = torch.empty((c, n), dtype=torch.float64, device=dev)
-        E64 = torch.empty((c,), dtype=torch.float64, device=dev)
-        sdev.fill(dm, 0, O64, G64, E64, stream.cuda_stream)
-        s64 = blm.Step(n, wl.block_offsets, wl.n_keep, stream=stream.cuda_stream)
+        import numpy as np
+        mixed_blocks = [step.block(b) for b in range(wl.n_blocks)]
+        mixed_dmu = dmu.cpu().numpy()
+        mixed_Sc, mixed_Hc = step.combined()
+        step.close()
+        s64 = blm.Step(n, wl.block_offsets, wl.n_keep, precision=blm.BLM_PREC_F64,
+                       input_type=blm.BLM_IN_F32, stream=stream.cuda_stream)
         d64 = torch.empty(n, dtype=torch.float64, device=dev)
         blm.blm_profile(s64.h, 1)
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
-        s64.accumulate(O64, G64, E64)
+        for s0 in range(0, ns, chunk):
+            c = min(chunk, ns - s0)
+            s64.accumulate(O[s0:s0 + c], G[s0:s0 + c], E[s0:s0 + c])
         s64.block_solve()
-        s64.project(O64, G64, E64)
-        s64.combined_solve(d64)
+        for s0 in range(0, ns, chunk):
+            c = min(chunk, ns - s0)
+            s64.project(O[s0:s0 + c], G[s0:s0 + c], E[s0:s0 + c])
+        e64 = s64.combined_solve(d64)
         t1.record(stream)
         torch.cuda.synchronize()
-        p64 = blm.blm_profile_read(s64.h)
         total = t0.elapsed_time(t1)
-        sweeps = sum(p64[k][0] for k in ("reference_shift", "first_moments", "contract_f64",
-                                          "project"))
-        solves = total - sweeps
-        scaled = sweeps * (ns / c) + solves
-        res["fp64_path"] = {"ms_per_step_scaled": round(scaled, 1), "measured_samples": c,
-                            "measured_ms": round(total, 1), "sweep_ms": round(sweeps, 1),
-                            "solve_ms": round(solves, 1),
-                            "speedup_mixed_over_fp64": round(scaled / ms_step, 2)}
+        res["fp64_path"] = {"ms_per_step": round(total, 1), "samples": ns,
+                            "speedup_mixed_over_fp64": round(total / ms_step, 2),
+                            "phases_ms": {k: round(v[0], 1) for k, v in
+                                          blm.blm_profile_read(s64.h).items() if v[1]}}
+        blocks64 = [s64.block(b) for b in range(wl.n_blocks)]
+        Sc64, Hc64 = s64.combined()
         s64.close()
-        # "+hist": the same FP64 step with N_O = 3 history directions (seeded unit rows), which
-        # adds the Theta projections and their sums (Eq. 9-10) to the first sweep
-        import numpy as np
-        n_old = 3
-        rng = np.random.default_rng(12345)
-        D = rng.standard_normal((n_old, n))
-        D /= np.linalg.norm(D, axis=1, keepdims=True)
-        sh = blm.Step(n, wl.block_offsets, wl.n_keep, n_old=n_old, old_dirs=D,
-                      stream=stream.cuda_stream)
-        blm.blm_profile(sh.h, 1)
-        torch.cuda.synchronize()
-        t0.record(stream)
-        sh.accumulate(O64, G64, E64)
-        sh.block_solve()
-        sh.project(O64, G64, E64)
-        sh.combined_solve(d64)
-        t1.record(stream)
-        torch.cuda.synchronize()
-        ph = blm.blm_profile_read(sh.h)
-        total_h = t0.elapsed_time(t1)
-        sweeps_h = sum(ph[k][0] for k in ("reference_shift", "first_moments", "contract_f64",
-                                           "project", "history_terms"))
-        res["fp64_hist"] = {"n_old": n_old, "measured_samples": c, "measured_ms": round(total_h, 1),
-                            "history_terms_ms": round(ph["history_terms"][0], 1),
-                            "ms_per_step_scaled": round(sweeps_h * (ns / c) + (total_h - sweeps_h), 1)}
-        sh.close()
+        res["err_vs_fp64"] = error_vs_fp64(wl, mixed_blocks, blocks64, res["e_pred"], e64,
+                                           mixed_dmu, d64.cpu().numpy(), mixed_Sc, mixed_Hc,
+                                           Sc64, Hc64)
+    else:
+        step.close()
     return res
+
+
+def _corr_err(A, A_ref, S_ref):
+    d = np.sqrt(np.abs(np.diag(S_ref)))
+    return float(np.max(np.abs(A - A_ref) / np.outer(d, d)))
+
+
+def error_vs_fp64(wl, blocks, blocks64, e, e64, dmu, dmu64, Sc, Hc, Sc64, Hc64):
+    """Error of the mixed step against the FP64 GPU path on the same samples.  Matrix entries in
+    correlation scaling |dA_xy| / sqrt(S_xx S_yy) (H also divided by 1 + |H_00|); the mean
+    relative error of the overlap diagonal shows any systematic bias of the accumulation.  The
+    combined matrices of the two paths are built on their own B^(b), so their difference also
+    carries the difference of the retained directions."""
+    em, bias = 0.0, []
+    for (S, H, lam, B), (S64, H64, lam64, B64) in zip(blocks, blocks64):
+        h0 = 1.0 + abs(H64[0, 0])
+        em = max(em, _corr_err(S, S64, S64), _corr_err(H, H64, S64) / h0)
+        bias.append(np.mean((np.diag(S)[1:] - np.diag(S64)[1:]) / np.diag(S64)[1:]))
+    dd = float(np.linalg.norm(dmu - dmu64) / np.linalg.norm(dmu64))
+    ec = max(_corr_err(Sc, Sc64, Sc64), _corr_err(Hc, Hc64, Sc64) / (1.0 + abs(Hc64[0, 0])))
+    return {"S_b_H_b": float("%.3g" % em), "S_b_diag_bias": float("%.3g" % np.mean(bias)),
+            "e_pred_hartree": float("%.3g" % abs(e - e64)), "dmu_rel": float("%.3g" % dd),
+            "S_c_H_c_incl_B_difference": float("%.3g" % ec),
+            "targets": {"S_b_H_b": 1e-6, "e_pred_hartree": 1e-8}}
+
+
+def run_error_scan(args):
+    """Error of the mixed step against the FP64 GPU path as the sample count grows: the same
+    resident samples (the workload's first N) through both paths, for each N of the scan.  The
+    zero-mean error of the hi/lo split falls as 1/sqrt(N); a systematic (accumulation) error
+    would not."""
+    import torch
+    import synth
+    from synth import device as sdev
+    import paper_1702_01481_gb300 as blm
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    wl = synth.workload(args.workload)
+    counts = sorted(int(x) for x in args.error_scan.split(","))
+    ns_max, n, chunk = counts[-1], wl.n, wl.chunk
+    O = torch.empty((ns_max, n), dtype=torch.float32, device=dev)
+    G = torch.empty((ns_max, n), dtype=torch.float32, device=dev)
+    E = torch.empty((ns_max,), dtype=torch.float32, device=dev)
+    dm = sdev.DeviceModel(wl, dev)
+    for s0 in range(0, ns_max, 32768):
+        c = min(32768, ns_max - s0)
+        sdev.fill(dm, s0, O[s0:s0 + c], G[s0:s0 + c], E[s0:s0 + c])
+    torch.cuda.synchronize()
+
+    def step(prec, ns):
+        st = blm.Step(n, wl.block_offsets, wl.n_keep, precision=prec, input_type=blm.BLM_IN_F32)
+        for s0 in range(0, ns, chunk):
+            c = min(chunk, ns - s0)
+            st.accumulate(O[s0:s0 + c], G[s0:s0 + c], E[s0:s0 + c])
+        st.block_solve()
+        blocks = [st.block(b) for b in range(wl.n_blocks)]
+        for s0 in range(0, ns, chunk):
+            c = min(chunk, ns - s0)
+            st.project(O[s0:s0 + c], G[s0:s0 + c], E[s0:s0 + c])
+        d = torch.empty(n, dtype=torch.float64, device=dev)
+        e = st.combined_solve(d)
+        Sc, Hc = st.combined()
+        st.close()
+        return blocks, e, d.cpu().numpy(), Sc, Hc
+
+    out = []
+    for ns in counts:
+        bm, em, dmm, Scm, Hcm = step(blm.BLM_PREC_BF16X4, ns)
+        b64, e64, d64, Sc64, Hc64 = step(blm.BLM_PREC_F64, ns)
+        r = error_vs_fp64(wl, bm, b64, em, e64, dmm, d64, Scm, Hcm, Sc64, Hc64)
+        r.pop("targets")
+        r["samples"] = ns
+        out.append(r)
+        print(json.dumps(r), file=sys.stderr)
+    return {"workload": args.workload, "scan": out}
 
 
 def run_e2e(args):
@@ -415,6 +472,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--error-scan", default="",
+                    help="comma-separated sample counts: print the mixed step's error against "
+                         "the FP64 GPU path at each (no timing)")
     args = ap.parse_args()
     if args.precision is None:
         args.precision = "bf16x4" if args.workload == "n16384" else "f64"
@@ -457,6 +517,9 @@ def main():
         print(json.dumps(line))
         return
 
+    if args.error_scan:
+        print(json.dumps(run_error_scan(args)))
+        return
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
@@ -480,8 +543,8 @@ def main():
         line["tc_pass1"] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in res["tc_pass1"].items()}
     if "fp64_path" in res:
         line["fp64_path"] = res["fp64_path"]
-    if "fp64_hist" in res:
-        line["fp64_hist"] = res["fp64_hist"]
+    if "err_vs_fp64" in res:
+        line["err_vs_fp64"] = res["err_vs_fp64"]
     if not args.no_e2e and world == 1:
         line["e2e"] = run_e2e(args)
     else:

@@ -65,6 +65,8 @@ typedef enum {
                           three products hi*hi + hi*lo + lo*hi on kind::tf32                 */
 } blm_precision;
 
+/* Element type of the sample arrays.  The tensor-core precisions take FP32 samples; the FP64
+ * path takes either (FP32 values are widened to FP64 on load). */
 typedef enum { BLM_IN_F64 = 0, BLM_IN_F32 = 1 } blm_input_type;
 
 typedef struct {
@@ -74,7 +76,7 @@ typedef struct {
                                      block b is parameters [off[b], off[b+1]) (contiguous)   */
   int32_t n_keep;                 /* N_K: directions kept per block (min(N_K, M_b) used)     */
   int32_t n_old;                  /* N_O: previous-update directions (Eq. 9), 0 = none; 0..16,
-                                     N_O > 0 needs precision BLM_PREC_F64 (FP64 input)       */
+                                     N_O > 0 needs precision BLM_PREC_F64                    */
   const double* old_dirs;         /* host or device, n_old x n_params row-major: row j is the
                                      overall update of iteration n-j (Sec. II.B); block k's
                                      slice of row j is D_jk.  Copied at blm_create.          */
@@ -170,8 +172,10 @@ const char* blm_profile_class_name(int i);
  * BLM_ERR_ARG with a message on stderr.  The first call on each device looks up the array's
  * device address (cudaGetSymbolAddress) with that device current; make that first call before
  * any stream capture.  Every call shares the one array: calls that overlap on the GPU (other
- * streams, other threads) race and must be serialised by the caller.  Runs on `stream` and
- * synchronises it; BLM_ERR_NUMERIC if the overlap is not positive definite or the solve fails. */
+ * streams, other threads) race and must be serialised by the caller.  Runs on `stream`, then
+ * copies its status word to the host and synchronises `stream` before it returns;
+ * BLM_ERR_NUMERIC if the overlap is not positive definite, the solve fails, or a kept direction
+ * has a zero or non-finite norm. */
 int32_t blm_noalloc_max_dim(void);
 blm_status blm_block_solve_noalloc(const double* S, const double* H, int32_t dim, int32_t n_keep,
                                    double* lambda, double* B, void* stream);

@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "blm_internal.cuh"
@@ -454,9 +455,10 @@ blm_status accumulate_dev(blm_handle* h, const T* O, const T* G, const T* E, con
     launch_sums<T>(O, G, E, w, ns, ld, ld, h->n, h->d_shift, h->d_vec, h->d_vec + h->n,
                    h->d_vec + 2 * h->n, h->d_scal, mixed, st);
   }
-  if constexpr (sizeof(T) == 8) {
-    // FP64 path (FP64 inputs): block contractions and history terms on CUDA cores
-    SrcArgs src{{O, nullptr}, {G, nullptr}, {ld, 0}, h->d_shift, E, w};
+  if (h->prec == BLM_PREC_F64) {
+    // FP64 path (FP64 inputs, or FP32 inputs widened on load): block contractions and history
+    // terms on CUDA cores
+    SrcArgs<T> src{O, nullptr, G, nullptr, {ld, 0}, h->d_shift, E, w};
     {
       Prof pr(h, PC_CONTRACT);
       launch_contract(h->d_seg1, h->d_tile1, h->ntile1, src, ns, pick_splits(h->ntile1, ns, 512),
@@ -474,11 +476,11 @@ blm_status accumulate_dev(blm_handle* h, const T* O, const T* G, const T* E, con
         const T* ws = w ? w + s0 : nullptr;
         // t_jk = O'_k . D_jk and u_jk = G_k . D_jk (Eq. 9 ratios) for every block k
         Prof pr(h, PC_HIST, 3);
-        launch_project<double, double>(Os, Gs, ld, ld, h->d_shift, nullptr, h->d_pbD, h->nb, nullptr, TY,
-                                       TZ, R, cnt, h->maxM, h->n_old, st);
-        launch_sums<double>(TY, TZ, Es, ws, cnt, R, R, R, nullptr, h->d_hvec, h->d_hvec + R,
-                            h->d_hvec + 2 * R, nullptr, false, st);
-        SrcArgs hs{{Os, TY}, {Gs, TZ}, {ld, R}, h->d_shift, Es, ws};
+        launch_project<T, double>(Os, Gs, ld, ld, h->d_shift, nullptr, h->d_pbD, h->nb, nullptr, TY,
+                                  TZ, R, cnt, h->maxM, h->n_old, st);
+        launch_sums_mixed<T>(TY, TZ, Es, ws, cnt, R, h->d_hvec, h->d_hvec + R, h->d_hvec + 2 * R,
+                             st);
+        SrcArgs<T> hs{Os, TY, Gs, TZ, {ld, R}, h->d_shift, Es, ws};
         launch_contract(h->d_segh, h->d_tileh, h->ntileh, hs, cnt,
                         pick_splits(h->ntileh, cnt, 512), st);
       }
@@ -523,22 +525,23 @@ blm_status project_dev(blm_handle* h, const T* O, const T* G, const T* E, const 
     const T* Gs = G + s0 * ld;
     const T* Es = E + s0;
     const T* ws = w ? w + s0 : nullptr;
-    if constexpr (sizeof(T) == 8) {
+    if (h->prec == BLM_PREC_F64) {
       // p_bj = Obar_b . B_j (centred with the first sweep's mean) and r_bj = G_b . B_j (Eq. 6)
       double* PY = (double*)h->d_scrY;
       double* PZ = (double*)h->d_scrZ;
       {
         Prof pr(h, PC_PROJECT, 2);
-        launch_project<double, double>(Os, Gs, ld, ld, h->d_shift, nullptr, h->d_pbB, h->nb, h->d_cen, PY,
-                                       PZ, dc, cnt, h->maxM, h->maxK, st);
-        launch_sums<double>(PY, PZ, Es, ws, cnt, dc, dc, dc, nullptr, h->d_cvec, h->d_cvec + dc,
-                            h->d_cvec + 2 * dc, nullptr, false, st);
+        launch_project<T, double>(Os, Gs, ld, ld, h->d_shift, nullptr, h->d_pbB, h->nb, h->d_cen, PY,
+                                  PZ, dc, cnt, h->maxM, h->maxK, st);
+        launch_sums_mixed<T>(PY, PZ, Es, ws, cnt, dc, h->d_cvec, h->d_cvec + dc,
+                             h->d_cvec + 2 * dc, st);
       }
-      SrcArgs cs{{nullptr, PY}, {nullptr, PZ}, {0, dc}, nullptr, Es, ws};
+      SrcArgs<T> cs{nullptr, PY, nullptr, PZ, {0, dc}, nullptr, Es, ws};
       Prof pr(h, PC_CONTRACT);
       launch_contract(h->d_segc, h->d_tilec, h->ntilec, cs, cnt,
                       pick_splits(h->ntilec, cnt, 512), st);
-    } else {
+    } else if constexpr (std::is_same<T, float>::value) {
+      // mixed paths (FP32 inputs only)
       float* PY = (float*)h->d_scrY;
       float* PZ = (float*)h->d_scrZ;
       const bool prepared = h->d_opA && dc <= h->n;
@@ -700,14 +703,6 @@ blm_status blm_create(const blm_problem* p, void* stream, blm_handle** out) {
   if (vs != BLM_OK) {
     fprintf(stderr, "blm_create: %s\n", why.c_str());
     return vs;
-  }
-  if (p->n_old > 0 && p->input_type != BLM_IN_F64) {
-    fprintf(stderr, "blm_create: history directions need FP64 inputs\n");
-    return BLM_ERR_UNSUPPORTED;
-  }
-  if (p->precision == BLM_PREC_F64 && p->input_type != BLM_IN_F64) {
-    fprintf(stderr, "blm_create: the FP64 path takes FP64 inputs\n");
-    return BLM_ERR_UNSUPPORTED;
   }
   blm_handle* h = new blm_handle();
   h->st = (cudaStream_t)stream;

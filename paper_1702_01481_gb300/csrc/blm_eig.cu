@@ -2170,8 +2170,9 @@ noalloc_block_kernel(double* scratch, const double* S, const double* H, int dim,
       int best = 0;
       for (int i = 1; i < m; ++i)
         if (fabs(v[i]) > fabs(v[best])) best = i;
-      red[0] = (n2 > 0.0) ? (v[best] < 0.0 ? -1.0 : 1.0) / sqrt(n2) : 0.0;
-      if (!(n2 > 0.0)) *status = ST_ZERO_DIR;
+      const bool ok = n2 > 0.0 && isfinite(n2);
+      red[0] = ok ? (v[best] < 0.0 ? -1.0 : 1.0) / sqrt(n2) : 0.0;
+      if (!ok) *status = ST_ZERO_DIR;
     }
     __syncthreads();
     const double sc = red[0];

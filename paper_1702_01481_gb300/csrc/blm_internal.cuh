@@ -24,13 +24,18 @@ struct Seg {
   int64_t col0;
 };
 
+// Source 0 holds the caller's samples (element type T: FP64, or FP32 widened to FP64 on load);
+// source 1 is FP64 scratch.  E and w are the caller's (type T).
+template <typename T>
 struct SrcArgs {
-  const double* Y[2];
-  const double* Z[2];
+  const T* Y0;
+  const double* Y1;
+  const T* Z0;
+  const double* Z1;
   int64_t ld[2];
   const double* shift;
-  const double* E;
-  const double* w;
+  const T* E;
+  const T* w;
 };
 
 // One 64 x 64 output tile: C[a0 + i, b0 + j] += sum_s w_s A(s, a0 + i) B(s, b0 + j),
@@ -70,7 +75,13 @@ void launch_sums(const T* Y, const T* Z, const T* E, const T* w, int64_t ns, int
                  int64_t ldz, int64_t ncols, const double* shift, double* sY, double* sEY,
                  double* sZ, double* scal /* [sw, sE] or NULL */, bool fp32_runs,
                  cudaStream_t st);
-void launch_contract(const Seg* segs, const Tile* tiles, int ntiles, const SrcArgs& src,
+// First moments of FP64 scratch columns (projections) with the caller's E and w (type TE):
+// sY += w Y, sEY += w E Y, sZ += w Z.
+template <typename TE>
+void launch_sums_mixed(const double* Y, const double* Z, const TE* E, const TE* w, int64_t ns,
+                       int64_t ncols, double* sY, double* sEY, double* sZ, cudaStream_t st);
+template <typename T>
+void launch_contract(const Seg* segs, const Tile* tiles, int ntiles, const SrcArgs<T>& src,
                      int64_t ns, int splits, cudaStream_t st);
 // Register-blocked FP32 projection (mixed path).  Returns false, launching nothing, where it
 // does not apply: more than 20 directions in a block, block offsets (offsets_aligned) or the

@@ -68,10 +68,10 @@ colsum_kernel(const T* __restrict__ O, int64_t ns, int64_t ld, int64_t n, int64_
 // 32 samples and the run sums added in FP64 when A = float (the mixed path, whose O' is the
 // FP32 value O - c); with A = double everything is FP64 (the FP64 path).
 // ---------------------------------------------------------------------------------------------
-template <typename T, typename A>
+template <typename T, typename A, typename TE = T>
 __global__ void __launch_bounds__(kThreads)
-sums_kernel(const T* __restrict__ Y, const T* __restrict__ Z, const T* __restrict__ E,
-            const T* __restrict__ w, int64_t ns, int64_t ldy, int64_t ldz, int64_t ncols,
+sums_kernel(const T* __restrict__ Y, const T* __restrict__ Z, const TE* __restrict__ E,
+            const TE* __restrict__ w, int64_t ns, int64_t ldy, int64_t ldz, int64_t ncols,
             int64_t per_split, const double* __restrict__ shift, double* __restrict__ sY,
             double* __restrict__ sEY, double* __restrict__ sZ, double* __restrict__ scal) {
   const int64_t col = (int64_t)blockIdx.x * kThreads + threadIdx.x;
@@ -120,18 +120,20 @@ sums_kernel(const T* __restrict__ Y, const T* __restrict__ Z, const T* __restric
 // Tiled FP64 contraction over samples: out[i, j] += sum_s w_s A(s, i) B(s, j), 64 x 64 tiles,
 // 16 samples per stage, 4 x 4 outputs per thread.  blockIdx.x = tile, blockIdx.y = sample split.
 // ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ double seg_value(const Seg& sg, const SrcArgs& a, int64_t s,
+template <typename T>
+__device__ __forceinline__ double seg_value(const Seg& sg, const SrcArgs<T>& a, int64_t s,
                                             int64_t c) {
   const int64_t col = sg.col0 + c;
-  const int64_t ld = a.ld[sg.src];
-  double y = a.Y[sg.src][s * ld + col];
+  const int64_t idx = s * a.ld[sg.src] + col;
+  double y = sg.src == 0 ? (double)a.Y0[idx] : a.Y1[idx];
   if (sg.src == 0 && a.shift) y -= a.shift[col];
-  if (sg.xform) y = a.E[s] * y + a.Z[sg.src][s * ld + col];
+  if (sg.xform) y = (double)a.E[s] * y + (sg.src == 0 ? (double)a.Z0[idx] : a.Z1[idx]);
   return y;
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kThreads)
-contract_kernel(const Seg* __restrict__ segs, const Tile* __restrict__ tiles, SrcArgs src,
+contract_kernel(const Seg* __restrict__ segs, const Tile* __restrict__ tiles, SrcArgs<T> src,
                 int64_t ns, int64_t per_split) {
   __shared__ double As[16][64];
   __shared__ double Bs[16][64];
@@ -157,7 +159,7 @@ contract_kernel(const Seg* __restrict__ segs, const Tile* __restrict__ tiles, Sr
         if (c < tl.a_n) av = seg_value(sa, src, s, tl.a0 + c);
         if (c < tl.b_n) {
           bv = seg_value(sb, src, s, tl.b0 + c);
-          if (src.w) bv *= src.w[s];
+          if (src.w) bv *= (double)src.w[s];
         }
       }
       As[k][c] = av;
@@ -624,7 +626,20 @@ void launch_sums(const T* Y, const T* Z, const T* E, const T* w, int64_t ns, int
                                                       sY, sEY, sZ, scal);
 }
 
-void launch_contract(const Seg* segs, const Tile* tiles, int ntiles, const SrcArgs& src,
+template <typename TE>
+void launch_sums_mixed(const double* Y, const double* Z, const TE* E, const TE* w, int64_t ns,
+                       int64_t ncols, double* sY, double* sEY, double* sZ, cudaStream_t st) {
+  if (ns <= 0) return;
+  const int64_t colblocks = (ncols + kThreads - 1) / kThreads;
+  const int splits = splits_for(ns, 256, (int64_t)4 * 152 * 4 / (colblocks > 0 ? colblocks : 1) + 1);
+  const int64_t per = ((ns + splits - 1) / splits + 31) / 32 * 32;
+  dim3 grid((unsigned)(colblocks > 0 ? colblocks : 1), (unsigned)splits);
+  sums_kernel<double, double, TE><<<grid, kThreads, 0, st>>>(Y, Z, E, w, ns, ncols, ncols, ncols,
+                                                              per, nullptr, sY, sEY, sZ, nullptr);
+}
+
+template <typename T>
+void launch_contract(const Seg* segs, const Tile* tiles, int ntiles, const SrcArgs<T>& src,
                      int64_t ns, int splits, cudaStream_t st) {
   if (ns <= 0 || ntiles <= 0) return;
   if (splits < 1) splits = 1;
@@ -632,7 +647,7 @@ void launch_contract(const Seg* segs, const Tile* tiles, int ntiles, const SrcAr
   per = (per + 15) / 16 * 16;
   splits = (int)((ns + per - 1) / per);
   dim3 grid((unsigned)ntiles, (unsigned)splits);
-  contract_kernel<<<grid, kThreads, 0, st>>>(segs, tiles, src, ns, per);
+  contract_kernel<T><<<grid, kThreads, 0, st>>>(segs, tiles, src, ns, per);
 }
 
 bool launch_project_rb(const float* O, const float* G, int64_t ld, const float* shift32,
@@ -717,5 +732,14 @@ template void launch_project<float, double>(const float*, const float*, int64_t,
                                             const double*, const float*, const ProjBlock*, int, const double*,
                                             double*, double*, int64_t, int64_t, int, int,
                                             cudaStream_t);
+template void launch_sums_mixed<double>(const double*, const double*, const double*,
+                                        const double*, int64_t, int64_t, double*, double*,
+                                        double*, cudaStream_t);
+template void launch_sums_mixed<float>(const double*, const double*, const float*, const float*,
+                                       int64_t, int64_t, double*, double*, double*, cudaStream_t);
+template void launch_contract<double>(const Seg*, const Tile*, int, const SrcArgs<double>&,
+                                      int64_t, int, cudaStream_t);
+template void launch_contract<float>(const Seg*, const Tile*, int, const SrcArgs<float>&,
+                                     int64_t, int, cudaStream_t);
 
 }  // namespace blm

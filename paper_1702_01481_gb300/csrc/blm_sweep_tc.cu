@@ -16,11 +16,12 @@
 //    stage of a unit alone, then `flush_stages` stages -- after which the epilogue warps add it
 //    into a second FP32 accumulator in tensor memory (L2, 256 columns, round-to-nearest CUDA-core
 //    adds), and at the end of each work unit add L2 + L1 into the FP64 result with atomics;
-//  * L1 does not restart from zero: the epilogue preloads it with minus half the partial sum the
-//    interval is expected to add (the running per-stage mean in L2 times the interval length),
-//    so D runs from about -P/2 to +P/2 and the truncations of its two halves cancel to first
-//    order.  The preloaded value is recomputed bit for bit from L2 when the interval is flushed
-//    and subtracted exactly.
+//  * L1 does not restart from zero: the epilogue preloads it with minus (q + 1) / (2 q) of the
+//    partial sum P the interval is expected to add (q = its K-steps; the expectation is the
+//    running per-stage mean in L2 times the interval length), so the values the accumulations
+//    produce are centred on zero and the truncations of the negative and positive halves cancel
+//    to first order (centre_frac).  The preloaded value is recomputed bit for bit from L2 when
+//    the interval is flushed and subtracted exactly.
 // Work units are (sample range, tile) pairs; a persistent grid of one CTA per SM walks them.
 //
 // Two kernels.  tc_op_kernel (the BF16X4 path) streams operand rows prepared once per element
@@ -37,7 +38,6 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
-#include <stdlib.h>
 
 #include "blm_internal.cuh"
 
@@ -61,6 +61,11 @@ constexpr int kConvWarps = 11;
 constexpr int kBarOffset = kStages * kStageBytes;
 constexpr int kSmemBytes = kBarOffset + 256 + 1024;   // + barriers + alignment slack
 constexpr uint32_t kWaitLimit = 1u << 24;          // polls (each try_wait may suspend briefly)
+// Samples per tensor-memory accumulator interval (after the first stage of a unit, which is
+// flushed alone): 128, i.e. 32 accumulations of the four split products.
+constexpr int kFlushSamples = 128;
+// Shortest sample range of a work unit (see the launchers).
+constexpr int64_t kMinUnitSamples = 2048;
 
 enum { A_VIEW = 0, A_FROM_B = 1, A_SEPARATE = 2 };
 
@@ -69,7 +74,7 @@ struct Bars {
   uint64_t op_empty[4];
   uint64_t l1_full;
   uint64_t l1_empty;
-  uint64_t db_full[2];       // prepared-operand kernel: double-buffered accumulator
+  uint64_t db_full[2];       // prepared-operand kernel: [0] HH interval drained, [1] CR of a unit
   uint64_t db_empty[2];
   uint64_t drain;
   uint32_t tmem_base;
@@ -204,6 +209,24 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),       \
                "r"(r[7])                                                                          \
                : "memory")
+
+#define TMEM_LD16(taddr, r)                                                                       \
+  asm volatile(                                                                                   \
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"    \
+      "%14,%15}, [%16];"                                                                          \
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),       \
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),   \
+        "=r"(r[14]), "=r"(r[15])                                                                  \
+      : "r"(taddr))
+
+#define TMEM_ST16(taddr, r)                                                                       \
+  asm volatile(                                                                                   \
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13," \
+      "%14,%15,%16};" ::"r"(taddr),                                                               \
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),     \
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),          \
+      "r"(r[15])                                                                                  \
+      : "memory")
 
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -427,10 +450,19 @@ __device__ __forceinline__ int interval_count(int nst, int fs) {
 __device__ __forceinline__ int interval_len(int i, int nst, int fs) {
   return i == 0 ? 1 : min(fs, nst - 1 - (i - 1) * fs);
 }
-// Preload factor of interval i >= 1: L1 starts at coef * L2, L2 holding the sum of the previous
-// stages_done = 1 + (i - 1) fs stages, so that L1 starts at -1/2 of the expected partial sum.
-__device__ __forceinline__ float preload_coef(int i, int nst, int fs) {
-  return -0.5f * (float)interval_len(i, nst, fs) / (float)(1 + (i - 1) * fs);
+// Where the preload puts the accumulator.  An interval of q K-steps (q hi*hi products, each
+// followed by its correction products at about the same value) takes the accumulator from d to
+// d + P in q equal increments, and every accumulation truncates relative to the value it
+// produces: the q levels d + P/q, .., d + P average d + P (q + 1) / (2 q).  Starting at
+// d = -P (q + 1) / (2 q) centres them on zero, so the truncations of the negative and positive
+// halves cancel to first order.  Returns (q + 1) / (2 q).
+__device__ __forceinline__ float centre_frac(int q) { return 0.5f + 0.5f / (float)q; }
+
+// Preload factor of interval i >= 1 (kq K-steps per stage): L1 starts at coef * L2, L2 holding
+// the sum of the previous stages_done = 1 + (i - 1) fs stages.
+__device__ __forceinline__ float preload_coef(int i, int nst, int fs, int kq) {
+  const int len = interval_len(i, nst, fs);
+  return -centre_frac(kq * len) * (float)len / (float)(1 + (i - 1) * fs);
 }
 
 // Epilogue role of tc_accumulate_kernel (warps 4-7, one per 32-lane tensor-memory quadrant): at
@@ -454,8 +486,9 @@ __device__ __forceinline__ void epilogue_role(const Params& P, Bars* bars, uint3
       if (!alive) break;
       tc_fence_after();
       const bool first = it == 0, last = it == nint - 1;
-      const float c_this = first ? 0.0f : preload_coef(it, nst, fs);
-      const float c_next = last ? 0.0f : preload_coef(it + 1, nst, fs);
+      // four K-steps per stage: 64 BF16 samples of K = 16, or 32 TF32 samples of K = 8
+      const float c_this = first ? 0.0f : preload_coef(it, nst, fs, 4);
+      const float c_next = last ? 0.0f : preload_coef(it + 1, nst, fs, 4);
       const int row = 32 * q + lane;
       const bool vrow = row < ti.nA;
       for (int cc = 0; cc < 256; cc += 32) {
@@ -658,43 +691,46 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
 }
 
 // ---------------------------------------------------------------------------------------------
-// Double-buffered accumulation for tc_op_kernel.  The MMA warp alternates between two 256-column
-// FP32 accumulators in tensor memory (buffer = global interval count & 1), so it never waits for
-// the drain of the interval it just finished.  The running FP32 sum of a work unit lives in the
-// registers of eight epilogue warps (warps 2-9: two per 32-lane quadrant, 128 columns each,
-// U[128] per thread) instead of in tensor memory.
+// Split accumulation for tc_op_kernel.  Tensor memory holds two 256-column FP32 accumulators:
+//   HH (columns 0-255)   the hi*hi products, in preloaded intervals of kFlushSamples samples;
+//   CR (columns 256-511) the correction products hi*lo + lo*hi + lo*lo of the whole work unit.
+// The tensor core aligns the terms of every accumulation to the accumulator's magnitude and
+// truncates the bits below that grid, so a product far smaller than the accumulator loses a
+// fraction of itself, always toward zero.  The corrections are 2^-8 (hi*lo, lo*hi) and 2^-16
+// (lo*lo) of the hi*hi terms; added into the large HH accumulator, the lo*lo terms -- positive on
+// the diagonal of every overlap block -- were partly cut off, a bias of about -3e-7 relative on
+// the diagonal of S_b.  In CR they meet an accumulator of their own size (hi*lo and lo*hi have
+// random signs, so CR stays near 2^-8 sqrt(N) of a single product), where the grid is fine.
 //
-// The rounding-bias correction keeps its form: interval 0 (the first stage alone) starts from
-// zero, interval i >= 1 from a preload d_i, about -1/2 of the partial sum it is expected to add,
-// written into its buffer when interval i - 2 (same buffer) is drained -- interval 1's, from
-// interval 0, in the drain of interval 0, which the MMA warp waits for once per unit.  The
-// preload is not recomputed at the next drain: the epilogue keeps U = sum of drained values -
-// sum of written preloads, i.e. at the drain of interval i with value V,
-//     s = U + V,  d = kappa_i s,  write d as interval i + 2's start,  U = s - d,
-// so that after the unit's last drain (no preload pending) U is the unit's sum.  Before the
-// drain U + V is the true running total minus the pending preload of interval i + 1, which
-// kappa_i accounts for when it turns s into the expected per-stage partial.
+// HH: interval 0 (the first stage alone) starts from zero, interval i >= 1 from a preload d_i of
+// about -(q + 1) / (2 q) of the partial sum it is expected to add (q = its K-steps, centre_frac),
+// written into the buffer by the epilogue when it drains interval i - 1.  The epilogue keeps, in
+// registers, U = sum of drained values - sum of written preloads; since every preload is drained
+// before the next is written, U + V at the drain of interval i is the exact running total s,
+// d_{i+1} = kappa_i s with kappa_i = -(q + 1) / (2 q) len(i + 1) / stages_through(i), and
+// U <- s - d_{i+1}.  After the unit's last drain U is the hi*hi sum; CR is then added once.
+// The MMA warp issues each stage's corrections before its hi*hi products, so that while the
+// epilogue drains HH at an interval boundary the tensor pipe works on CR.
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ int stages_through(int i, int nst, int fs) {
   return i == 0 ? 1 : min(nst, 1 + i * fs);
 }
-__device__ __forceinline__ float db_kappa(int i, int nst, int fs) {
-  const float pending = (i >= 1) ? 0.5f * (float)interval_len(i + 1, nst, fs) : 0.0f;
-  // (at i = 0 interval 1's preload is written in the same drain, so nothing is pending yet)
-  return -0.5f * (float)interval_len(i + 2, nst, fs) /
-         ((float)stages_through(i, nst, fs) + pending);
+// Two K-steps (of 16 samples) per 32-sample stage: an interval of len stages has 2 len levels.
+__device__ __forceinline__ float split_kappa(int i, int nst, int fs) {
+  const int len = interval_len(i + 1, nst, fs);
+  return -centre_frac(2 * len) * (float)len / (float)stages_through(i, nst, fs);
 }
 
-__device__ __forceinline__ void epilogue_db_role(const Params& P, Bars* bars, uint32_t tmem,
-                                                 int warp, int lane, int fs) {
+__device__ __forceinline__ void epilogue_split_role(const Params& P, Bars* bars, uint32_t tmem,
+                                                    int warp, int lane, int fs) {
   const int q = warp & 3;                          // tensor-memory lane quadrant
   const int h = (warp - 2) >> 2;                   // warps 2-5: columns 0-127, 6-9: 128-255
   const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(128 * h);
   const int row = 32 * q + lane;
-  uint32_t k = 0;
+  uint32_t k = 0, j = 0;
   bool alive = true;
   float U[128];
-  for (int64_t u = blockIdx.x; u < P.nunits && alive; u += gridDim.x) {
+  for (int64_t u = blockIdx.x; u < P.nunits && alive; u += gridDim.x, ++j) {
     const int64_t sa = (u / P.ntiles) * P.range_len;
     const int64_t sb = min(P.ns, sa + P.range_len);
     const int nst = (int)((sb - sa + kTmaStageK - 1) / kTmaStageK);
@@ -702,45 +738,61 @@ __device__ __forceinline__ void epilogue_db_role(const Params& P, Bars* bars, ui
 #pragma unroll
     for (int i = 0; i < 128; ++i) U[i] = 0.0f;
     for (int it = 0; it < nint; ++it, ++k) {
-      const uint32_t b = k & 1;
-      alive = mbar_wait(&bars->db_full[b], (k >> 1) & 1, bars, P.err, 13);
+      alive = mbar_wait(&bars->db_full[0], k & 1, bars, P.err, 13);
       if (!alive) break;
       tc_fence_after();
-      const bool pre = it + 2 < nint;
-      const float kap = pre ? db_kappa(it, nst, fs) : 0.0f;
-      // interval 1 starts from a preload too, formed from interval 0 (the MMA warp waits for
-      // this drain before interval 1): it goes into the other buffer
-      const bool pre1 = it == 0 && nint > 1;
-      const float kap1 = pre1 ? -0.5f * (float)interval_len(1, nst, fs) : 0.0f;
+      const bool pre = it + 1 < nint;
+      const float kap = pre ? split_kappa(it, nst, fs) : 0.0f;
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        uint32_t a[8], a1[8];
-        TMEM_LD8(lane_addr + b * 256 + 8 * c, a);
+      for (int c = 0; c < 16; c += 2) {
+        uint32_t a[8], b[8];
+        TMEM_LD8(lane_addr + 8 * c, a);
+        TMEM_LD8(lane_addr + 8 * c + 8, b);
         tmem_wait_ld();
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const float s = U[8 * c + i] + __uint_as_float(a[i]);
-          const float d = kap * s, d1 = kap1 * s;
-          U[8 * c + i] = (s - d) - d1;
+          const float d = kap * s;
+          U[8 * c + i] = s - d;
           a[i] = __float_as_uint(d);
-          a1[i] = __float_as_uint(d1);
+          const float s1 = U[8 * c + 8 + i] + __uint_as_float(b[i]);
+          const float d1 = kap * s1;
+          U[8 * c + 8 + i] = s1 - d1;
+          b[i] = __float_as_uint(d1);
         }
-        if (pre) TMEM_ST8(lane_addr + b * 256 + 8 * c, a);
-        if (pre1) TMEM_ST8(lane_addr + (b ^ 1) * 256 + 8 * c, a1);
+        if (pre) {
+          TMEM_ST8(lane_addr + 8 * c, a);
+          TMEM_ST8(lane_addr + 8 * c + 8, b);
+        }
       }
-      if (pre || pre1) tmem_wait_st();
+      if (pre) tmem_wait_st();
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&bars->db_empty[b]);
-      if (it != nint - 1) continue;
-      const TileInfo ti = decode_tile(P.tiles[u % P.ntiles], P.w != nullptr);
-      if (row < ti.nA) {
-        double* orow = ti.out + (int64_t)(ti.row0 + row) * 2 * ti.m + ti.col0 + 128 * h;
-        const int ncol = min(128, ti.nB - 128 * h);
+      if (lane == 0) mbar_arrive(&bars->db_empty[0]);
+    }
+    if (!alive) break;
+    // the unit's corrections
+    alive = mbar_wait(&bars->db_full[1], j & 1, bars, P.err, 16);
+    if (!alive) break;
+    tc_fence_after();
 #pragma unroll
-        for (int i = 0; i < 128; ++i)
-          if (i < ncol) atomicAdd(orow + i, (double)U[i]);
-      }
+    for (int c = 0; c < 16; ++c) {
+      uint32_t a[8];
+      TMEM_LD8(lane_addr + 256 + 8 * c, a);
+      tmem_wait_ld();
+#pragma unroll
+      for (int i = 0; i < 8; ++i) U[8 * c + i] += __uint_as_float(a[i]);
+    }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&bars->db_empty[1]);
+    const TileInfo ti = decode_tile(P.tiles[u % P.ntiles], P.w != nullptr);
+    if (row < ti.nA) {
+      double* orow = ti.out + (int64_t)(ti.row0 + row) * 2 * ti.m + ti.col0 + 128 * h;
+      const int ncol = min(128, ti.nB - 128 * h);
+#pragma unroll
+      for (int i = 0; i < 128; ++i)
+        if (i < ncol) atomicAdd(orow + i, (double)U[i]);
     }
   }
 }
@@ -751,8 +803,8 @@ __device__ __forceinline__ void epilogue_db_role(const Params& P, Bars* bars, ui
 // and 32-sample group holding [hi(32) | lo(32)] -- so this kernel only streams them: warp 1 loads
 // each stage's B rows (256 x 128 bytes) and, unless A is a view of B, its A rows (128 x 128
 // bytes) with 128-byte-swizzled cp.async.bulk.tensor into a four-deep ring; warp 0 issues the
-// four products of two K steps into one of two tensor-memory accumulators; warps 2-9 are the
-// epilogue (epilogue_db_role).  No converter warps.
+// products of two K steps into the HH and CR accumulators; warps 2-9 are the epilogue
+// (epilogue_split_role).  No converter warps.
 // ---------------------------------------------------------------------------------------------
 constexpr int kOpStagesP = 4;
 constexpr int kPStageBytes = (kBRows + kARows) * 128;          // 48 KB
@@ -797,9 +849,9 @@ tc_op_kernel(const Params P, const __grid_constant__ CUtensorMap mapA,
 
   if (warp == 0) {
     // ------------------------------- MMA issuer -------------------------------
-    uint32_t g = 0, k = 0;
+    uint32_t g = 0, k = 0, j = 0;
     bool alive = true;
-    for (int64_t u = blockIdx.x; u < P.nunits && alive; u += gridDim.x) {
+    for (int64_t u = blockIdx.x; u < P.nunits && alive; u += gridDim.x, ++j) {
       const TileInfo ti = decode_tile(P.tiles[u % P.ntiles], P.w != nullptr);
       const int64_t sa = (u / P.ntiles) * P.range_len;
       const int64_t sb = min(P.ns, sa + P.range_len);
@@ -809,34 +861,48 @@ tc_op_kernel(const Params P, const __grid_constant__ CUtensorMap mapA,
         uint32_t acc = 1;
         const bool istart = (st == 0) || ((st - 1) % fs == 0);
         const bool iend = (st == 0) || ((st - 1) % fs == fs - 1) || (st == nst - 1);
-        const uint32_t dacc = tmem + (k & 1) * 256u;   // this interval's accumulator
-        if (istart) {
-          alive = mbar_wait(&bars->db_empty[k & 1], ((k >> 1) & 1) ^ 1, bars, P.err, 11);
+        if (alive && st == 0) {
+          // the unit's first correction product overwrites CR: the previous unit's CR must
+          // have been read
+          alive = mbar_wait(&bars->db_empty[1], (j & 1) ^ 1, bars, P.err, 17);
           tc_fence_after();
-          // interval 0 of a unit starts from zero, later ones from the epilogue's preload;
-          // interval 1's preload comes from interval 0, so wait for that drain as well
-          if (alive && st == 1)
-            alive = mbar_wait(&bars->db_empty[(k - 1) & 1], ((k - 1) >> 1) & 1, bars, P.err, 14);
-          acc = (st == 0) ? 0 : 1;
         }
         if (alive) alive = mbar_wait(&bars->op_full[slot], use & 1, bars, P.err, 12);
         if (!alive) break;
         tc_fence_after();
+        const uint32_t ob = smem_u32(smem + slot * kPStageBytes);
+        const uint32_t oa = (ti.amode == A_VIEW) ? ob + (uint32_t)(ti.row0 - ti.pb) * 128u
+                                                 : ob + (uint32_t)kBRows * 128u;
         if (lane == 0) {
-          const uint32_t ob = smem_u32(smem + slot * kPStageBytes);
-          const uint32_t oa = (ti.amode == A_VIEW) ? ob + (uint32_t)(ti.row0 - ti.pb) * 128u
-                                                   : ob + (uint32_t)kBRows * 128u;
+          // corrections first: they keep the tensor pipe busy while HH is drained
 #pragma unroll
           for (int ks = 0; ks < 2; ++ks) {
             const uint32_t o = ks * 32;
-            mma_bf16(dacc, sdesc(oa + o), sdesc(ob + o), acc);           // hi * hi
-            mma_bf16(dacc, sdesc(oa + o), sdesc(ob + 64 + o), 1);        // hi * lo
-            mma_bf16(dacc, sdesc(oa + 64 + o), sdesc(ob + o), 1);        // lo * hi
-            mma_bf16(dacc, sdesc(oa + 64 + o), sdesc(ob + 64 + o), 1);   // lo * lo
-            acc = 1;
+            mma_bf16(tmem + 256u, sdesc(oa + o), sdesc(ob + 64 + o),              // hi * lo
+                     (st == 0 && ks == 0) ? 0u : 1u);
+            mma_bf16(tmem + 256u, sdesc(oa + 64 + o), sdesc(ob + o), 1);        // lo * hi
+            mma_bf16(tmem + 256u, sdesc(oa + 64 + o), sdesc(ob + 64 + o), 1);   // lo * lo
+          }
+        }
+        __syncwarp();
+        if (istart) {
+          // interval 0 of a unit starts HH from zero, later intervals from the epilogue's
+          // preload: either way the previous interval's drain must be complete
+          alive = mbar_wait(&bars->db_empty[0], (k & 1) ^ 1, bars, P.err, 11);
+          tc_fence_after();
+          acc = (st == 0) ? 0 : 1;
+        }
+        if (lane == 0) {
+          if (alive) {
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+              mma_bf16(tmem, sdesc(oa + ks * 32), sdesc(ob + ks * 32), acc);   // hi * hi
+              acc = 1;
+            }
           }
           mma_commit(&bars->op_empty[slot]);
-          if (iend) mma_commit(&bars->db_full[k & 1]);
+          if (alive && iend) mma_commit(&bars->db_full[0]);
+          if (alive && st == nst - 1) mma_commit(&bars->db_full[1]);
         }
         __syncwarp();
         if (iend) ++k;
@@ -882,7 +948,7 @@ tc_op_kernel(const Params P, const __grid_constant__ CUtensorMap mapA,
         }
       }
   } else if (warp >= 2 && warp < 10) {
-    epilogue_db_role(P, bars, tmem, warp, lane, fs);
+    epilogue_split_role(P, bars, tmem, warp, lane, fs);
   }
 
   tc_fence_before();
@@ -950,20 +1016,15 @@ cudaError_t launch_tc_accumulate(const float* Y, const float* Z, const float* E,
   P.ld = ld;
   P.tiles = tiles;
   P.ntiles = ntiles;
-  // sample ranges: enough units to keep every SM busy with a small tail
+  // sample ranges: enough units to keep every SM busy with a small tail, but never shorter
+  // than kMinUnitSamples, so that the preloaded intervals (not the unpreloaded first stage)
+  // carry nearly all of every unit's sum
   int64_t range = 8192;
   const int64_t sk = tf32 ? kStageKTf : kStageK;
-  while (range > sk && ((ns + range - 1) / range) * ntiles < 8LL * sms) range /= 2;
+  while (range > kMinUnitSamples && ((ns + range - 1) / range) * ntiles < 8LL * sms) range /= 2;
   P.range_len = range;
   P.nunits = ((ns + range - 1) / range) * ntiles;
-  // stages between restarts of the tensor-memory accumulator: 128 samples
-  static int flush = -1;
-  if (flush < 0) {
-    const char* env = getenv("BLM_TC_FLUSH_SAMPLES");
-    flush = env ? atoi(env) : 128;
-    if (flush < 32) flush = 32;
-  }
-  P.flush_stages = (int)(flush / sk) > 0 ? (int)(flush / sk) : 1;
+  P.flush_stages = (int)(kFlushSamples / sk) > 0 ? (int)(kFlushSamples / sk) : 1;
   P.err = err;
   P.vec_ok = (ld % 4 == 0) && (((uintptr_t)Y | (uintptr_t)Z) % 16 == 0);
   const int grid = (int)(P.nunits < sms ? P.nunits : sms);
@@ -1023,16 +1084,10 @@ cudaError_t launch_tc_prepared(const uint8_t* opA, const uint8_t* opBS, const ui
   // FP64 atomics and one wait for its first interval's drain, so units are kept long; at
   // least four units per SM keep the tail short
   int64_t range = 16384;
-  while (range > kTmaStageK && ((ns + range - 1) / range) * ntiles < 4LL * sms) range /= 2;
+  while (range > kMinUnitSamples && ((ns + range - 1) / range) * ntiles < 4LL * sms) range /= 2;
   P.range_len = range;
   P.nunits = ((ns + range - 1) / range) * ntiles;
-  static int flush = -1;
-  if (flush < 0) {
-    const char* env = getenv("BLM_TC_FLUSH_SAMPLES");
-    flush = env ? atoi(env) : 128;
-    if (flush < 32) flush = 32;
-  }
-  P.flush_stages = flush / kTmaStageK > 0 ? flush / kTmaStageK : 1;
+  P.flush_stages = kFlushSamples / kTmaStageK;
   P.err = err;
   P.vec_ok = 0;
   const int grid = (int)(P.nunits < sms ? P.nunits : sms);
