@@ -29,7 +29,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOADS = ("n16384", "n2048", "n200")
+WORKLOADS = ("n16384", "n16384u", "batch32", "n2048", "n200")
+PRECISIONS = {"bf16x4": "BLM_PREC_BF16X4", "tf32x4": "BLM_PREC_TF32X4", "f64": "BLM_PREC_F64"}
 
 
 def useful_flop_per_sample(wl):
@@ -143,7 +144,7 @@ def run_ours(args, rank, world):
     if args.samples:
         wl.n_samples = args.samples
     ns, n, chunk = wl.n_samples, wl.n, wl.chunk
-    mixed = args.precision == "bf16x4"
+    mixed = args.precision != "f64"
     dt = torch.float32 if mixed else torch.float64
     stream = torch.cuda.current_stream()
 
@@ -158,7 +159,7 @@ def run_ours(args, rank, world):
         sdev.fill(dm, s0, O[s0:s0 + c], G[s0:s0 + c], E[s0:s0 + c], stream.cuda_stream)
     torch.cuda.synchronize()
 
-    prec = blm.BLM_PREC_BF16X4 if mixed else blm.BLM_PREC_F64
+    prec = getattr(blm, PRECISIONS[args.precision])
     inp = blm.BLM_IN_F32 if mixed else blm.BLM_IN_F64
     step = blm.Step(n, wl.block_offsets, wl.n_keep, precision=prec, input_type=inp,
                     stream=stream.cuda_stream)
@@ -178,21 +179,39 @@ def run_ours(args, rank, world):
     for _ in range(args.warmup):
         e_pred = one_step()
     torch.cuda.synchronize()
+    if args.graph:
+        # per-kernel-class times from one profiled eager step (a captured graph records no
+        # events), then the whole step captured once and replayed in the timed region
+        blm.blm_profile(step.h, 1)
+        one_step()
+        prof = blm.blm_profile_read(step.h)
+        blm.blm_profile(step.h, 0)
+        prof = {k: (v[0] * args.steps, v[1] * args.steps) for k, v in prof.items()}
+        blm.blm_graph_capture(step.h, O, G, E, None, ns, chunk, n, dmu)
+        blm.blm_graph_launch(step.h)
+        e_pred = blm.blm_graph_result(step.h)
+        torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
-    blm.blm_profile(step.h, 1)
+    if not args.graph:
+        blm.blm_profile(step.h, 1)
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     start.record(stream)
     for _ in range(args.steps):
-        e_pred = one_step()
+        if args.graph:
+            blm.blm_graph_launch(step.h)
+            e_pred = blm.blm_graph_result(step.h)
+        else:
+            e_pred = one_step()
     end.record(stream)
     torch.cuda.synchronize()
-    prof = blm.blm_profile_read(step.h)
-    blm.blm_profile(step.h, 0)
+    if not args.graph:
+        prof = blm.blm_profile_read(step.h)
+        blm.blm_profile(step.h, 0)
     clk = clocks.stop()
     elapsed_ms = start.elapsed_time(end)
     flop = useful_flop_per_sample(wl) * ns
@@ -212,18 +231,23 @@ def run_ours(args, rank, world):
     ms1, l1 = prof.get("contract_tc_pass1", (0.0, 0))
     if l1:
         per_launch_samples = ns * res["steps"] / l1
-        exec_flop = 2 * 4 * tile_macs * per_launch_samples     # hi*hi + hi*lo + lo*hi + lo*lo
+        # executed products: hi*hi + hi*lo + lo*hi + lo*lo (both splits)
+        nprod = 4
+        exec_flop = 2 * nprod * tile_macs * per_launch_samples
         t_launch = ms1 / l1 / 1e3
         res["tc_pass1"] = {"ms_per_launch": round(ms1 / l1, 3), "launches": l1,
                            "hbm_gbs_algorithmic": round(2 * per_launch_samples * n * 4 / t_launch / 1e9, 1),
                            "tensor_tflops_executed": round(exec_flop / t_launch / 1e12, 1),
                            "useful_tflops": round(sum(3 * mb * mb for mb in m) * per_launch_samples / t_launch / 1e12, 1)}
     if kname == "contract_tc_pass1" and l1:
-        p = pk.get("bf16_tflops_sustained", 1700.0)
+        # TF32 runs at the nominal dense ratio 1.1 / 2.25 of the measured BF16 peak
+        p = pk.get("bf16_tflops_sustained", 1700.0) * (1.1 / 2.25 if args.precision == "tf32x4" else 1.0)
         ach = res["tc_pass1"]["tensor_tflops_executed"]
         roof = {"bound": "tensor", "achieved": ach, "peak": p, "unit": "TFLOP/s",
                 "frac": round(ach / p, 4), "traffic": profiled_traffic("tc_op_kernel_n16384.md"),
-                "kernel": "tc_op_kernel (first sweep, prepared operands)",
+                "kernel": ("tc_accumulate_kernel (first sweep, TF32 split converted in the kernel)"
+                           if args.precision == "tf32x4" else
+                           "tc_op_kernel (first sweep, prepared operands)"),
                 "per_launch_algorithmic_flop": exec_flop,
                 "peak_source": "measured bf16 sustained" if "bf16_tflops_sustained" in pk else "fallback"}
     elif kname == "contract_f64" and klaunch:
@@ -293,6 +317,42 @@ def run_ours(args, rank, world):
                                            Sc64, Hc64)
     else:
         step.close()
+    if mixed and not args.no_hist and rank == 0:
+        # "+hist": the same step with N_O = 3 history directions (seeded unit rows), whose
+        # projections and sums (Eq. 9-10) join the first sweep's tensor-core launch
+        n_old = 3
+        rng = np.random.default_rng(12345)
+        D = rng.standard_normal((n_old, n))
+        D /= np.linalg.norm(D, axis=1, keepdims=True)
+        sh = blm.Step(n, wl.block_offsets, wl.n_keep, n_old=n_old, old_dirs=D, precision=prec,
+                      input_type=inp, stream=stream.cuda_stream)
+
+        def hist_step():
+            sh.reset()
+            for s0 in range(0, ns, chunk):
+                c = min(chunk, ns - s0)
+                sh.accumulate(O[s0:s0 + c], G[s0:s0 + c], E[s0:s0 + c])
+            sh.block_solve()
+            for s0 in range(0, ns, chunk):
+                c = min(chunk, ns - s0)
+                sh.project(O[s0:s0 + c], G[s0:s0 + c], E[s0:s0 + c])
+            return sh.combined_solve(dmu)
+
+        hist_step()
+        blm.blm_profile(sh.h, 1)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record(stream)
+        hist_step()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ph = blm.blm_profile_read(sh.h)
+        res["mixed_hist"] = {"n_old": n_old, "ms_per_step": round(t0.elapsed_time(t1), 1),
+                             "history_projection_ms": round(ph["history_terms"][0], 1),
+                             "contract_tc_pass1_ms": round(ph["contract_tc_pass1"][0], 1),
+                             "eig_blocks_ms": round(ph["eig_blocks"][0], 1)}
+        sh.close()
     return res
 
 
@@ -371,6 +431,101 @@ def run_error_scan(args):
     return {"workload": args.workload, "scan": out}
 
 
+def run_batch(args):
+    """The batch of 32 independent optimisations: every problem's samples resident in HBM, each
+    problem's tiles chosen by the autotuner, one step of all 32 captured as one CUDA graph and
+    replayed per timed step."""
+    import torch
+    import synth
+    from synth import device as sdev
+    import paper_1702_01481_gb300 as blm
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    wls = synth.batch_workloads(32)
+    prec = getattr(blm, PRECISIONS[args.precision])
+    data = []
+    for wl in wls:
+        O = torch.empty((wl.n_samples, wl.n), dtype=torch.float32, device=dev)
+        G = torch.empty((wl.n_samples, wl.n), dtype=torch.float32, device=dev)
+        E = torch.empty((wl.n_samples,), dtype=torch.float32, device=dev)
+        dm = sdev.DeviceModel(wl, dev)
+        for s0 in range(0, wl.n_samples, 32768):
+            c = min(32768, wl.n_samples - s0)
+            sdev.fill(dm, s0, O[s0:s0 + c], G[s0:s0 + c], E[s0:s0 + c], stream.cuda_stream)
+        data.append((O, G, E))
+    torch.cuda.synchronize()
+    pass_samples = 8192
+    probs = [blm.make_problem(wl.n, wl.block_offsets, wl.n_keep, precision=prec,
+                              input_type=blm.BLM_IN_F32, pass_samples=pass_samples) for wl in wls]
+    b = blm.blm_batch_create(probs, stream.cuda_stream)
+    hs = [blm.blm_batch_handle(b, i) for i in range(len(wls))]
+    choices = [blm.blm_autotune(h, d[0], d[1], d[2], None, min(wl.n_samples, pass_samples), wl.n)
+               for h, d, wl in zip(hs, data, wls)]
+    # per-kernel-class device times: one profiled eager step of every problem
+    prof = {}
+    for h, (O, G, E), wl in zip(hs, data, wls):
+        blm.blm_profile(h, 1)
+        for s0 in range(0, wl.n_samples, wl.chunk):
+            blm.blm_accumulate(h, O[s0:s0 + wl.chunk], G[s0:s0 + wl.chunk], E[s0:s0 + wl.chunk], None,
+                               min(wl.chunk, wl.n_samples - s0), wl.n)
+        blm.blm_block_solve(h)
+        for s0 in range(0, wl.n_samples, wl.chunk):
+            blm.blm_project(h, O[s0:s0 + wl.chunk], G[s0:s0 + wl.chunk], E[s0:s0 + wl.chunk], None,
+                            min(wl.chunk, wl.n_samples - s0), wl.n)
+        d = torch.empty(wl.n, dtype=torch.float64, device=dev)
+        blm.blm_combined_solve(h, d)
+        for k, v in blm.blm_profile_read(h).items():
+            a = prof.get(k, (0.0, 0))
+            prof[k] = (a[0] + v[0], a[1] + v[1])
+        blm.blm_profile(h, 0)
+        blm.blm_reset(h)
+    dmu = [torch.empty(wl.n, dtype=torch.float64, device=dev) for wl in wls]
+    blm.blm_batch_capture(b, [d[0] for d in data], [d[1] for d in data], [d[2] for d in data], None,
+                          [wl.n_samples for wl in wls], [wl.n for wl in wls], 65536, dmu)
+    for _ in range(args.warmup):
+        blm.blm_batch_launch(b)
+        e, st, rc = blm.blm_batch_result(b, len(wls))
+        if rc != 0:
+            raise RuntimeError("batch step failed: statuses %s: %s"
+                               % (list(st), blm._lib.blm_batch_last_error(b).decode()))
+    torch.cuda.synchronize()
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for _ in range(args.steps):
+        blm.blm_batch_launch(b)
+        e, st, rc = blm.blm_batch_result(b, len(wls))
+    end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_step = start.elapsed_time(end) / args.steps
+    flop = sum(useful_flop_per_sample(wl) * wl.n_samples for wl in wls)
+    kname, (kms, kl) = max(prof.items(), key=lambda kv: kv[1][0])
+    pk = peaks()
+    roof = None
+    if kname == "eig_blocks":
+        d = [b1 - b0 + 1 for wl in wls for b0, b1 in zip(wl.block_offsets[:-1], wl.block_offsets[1:])]
+        fl = sum((1.0 / 3 + 2 + 10.0 / 3 + 10) * x ** 3 for x in d)
+        peak = 1.7 * 2 * 152 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        ach = fl / (kms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 3), "unit": "TFLOP/s",
+                "frac": round(ach / peak, 4), "traffic": None,
+                "kernel": "eig_kernel (FP64 block solves; summed over the problems' eager steps)",
+                "per_launch_algorithmic_flop": fl}
+    else:
+        roof = {"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": None, "kernel": kname, "note": "no roofline model for this class"}
+    blm.blm_batch_destroy(b)
+    return dict(ms_step=ms_step, value=flop / (ms_step / 1e3) / 1e9, clocks=clk, roofline=roof,
+                prof=prof, e_pred=[float(x) for x in e], choices=choices,
+                samples=sum(wl.n_samples for wl in wls),
+                gpu_launches=int(sum(v[1] for v in prof.values())), dominant=kname)
+
+
 def run_e2e(args):
     """Same metric through the C ABI with host (pinned) sample buffers: every step copies its
     samples host -> device inside the timed region and reads back Delta mu and E_pred."""
@@ -380,10 +535,11 @@ def run_e2e(args):
     import paper_1702_01481_gb300 as blm
 
     dev = torch.device("cuda", torch.cuda.current_device())
+    torch.cuda.empty_cache()           # the resident-sample run's memory goes back to the device
     wl = synth.workload(args.workload)
     ns = min(wl.n_samples, args.e2e_samples)
     n = wl.n
-    mixed = args.precision == "bf16x4"
+    mixed = args.precision != "f64"
     dt = torch.float32 if mixed else torch.float64
     O = torch.empty((ns, n), dtype=dt, pin_memory=True)
     G = torch.empty((ns, n), dtype=dt, pin_memory=True)
@@ -401,11 +557,14 @@ def run_e2e(args):
         E[s0:s0 + c].copy_(be[:c])
     del bo, bg, be
     torch.cuda.synchronize()
-    prec = blm.BLM_PREC_BF16X4 if mixed else blm.BLM_PREC_F64
+    prec = getattr(blm, PRECISIONS[args.precision])
     inp = blm.BLM_IN_F32 if mixed else blm.BLM_IN_F64
     stream = torch.cuda.current_stream()
     step = blm.Step(n, wl.block_offsets, wl.n_keep, precision=prec, input_type=inp,
                     stream=stream.cuda_stream)
+    # the first sweep's device copies serve the second sweep (one host-to-device copy of the
+    # samples per step)
+    blm.blm_set_host_cache(step.h, ns * (2 * n + 2) * O.element_size() + (64 << 20))
     dmu = torch.empty(n, dtype=torch.float64, pin_memory=True)
     chunk = wl.chunk
 
@@ -433,7 +592,7 @@ def run_e2e(args):
     sec = sorted(times)[len(times) // 2]
     step.close()
     flop = useful_flop_per_sample(wl) * ns
-    h2d = 2 * 2 * ns * n * O.element_size() + 2 * ns * E.element_size()
+    h2d = 2 * ns * n * O.element_size() + ns * E.element_size()
     return {"value": round(flop / sec / 1e9, 1), "unit": "sample-GFLOP/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 * n + 8,
             "samples_per_step": ns, "ms_per_step": round(sec * 1e3, 1),
@@ -464,32 +623,69 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="n16384", choices=WORKLOADS)
-    ap.add_argument("--precision", default=None, choices=["bf16x4", "f64"])
+    ap.add_argument("--precision", default=None, choices=list(PRECISIONS))
+    ap.add_argument("--graph", action="store_true",
+                    help="time the step as one captured CUDA graph (default for n16384u)")
     ap.add_argument("--samples", type=int, default=0)
     ap.add_argument("--cpu-samples", type=int, default=2048)
-    ap.add_argument("--e2e-samples", type=int, default=131072)
+    ap.add_argument("--e2e-samples", type=int, default=524288,
+                    help="samples of the end-to-end step (pinned host memory: 4 (2n + 1) bytes "
+                         "per sample, 69 GB at the default on the 16384-parameter workload)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-hist", action="store_true")
     ap.add_argument("--error-scan", default="",
                     help="comma-separated sample counts: print the mixed step's error against "
                          "the FP64 GPU path at each (no timing)")
     args = ap.parse_args()
     if args.precision is None:
-        args.precision = "bf16x4" if args.workload == "n16384" else "f64"
+        args.precision = {"n16384": "bf16x4", "n16384u": "tf32x4"}.get(args.workload, "f64")
+    if args.workload == "n16384u":
+        args.graph = True
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     import synth
+    if args.workload == "batch32":
+        if args.precision is None:
+            args.precision = "bf16x4"
+        if rank != 0:
+            return
+        r = run_batch(args)
+        line = {"metric": "blocked-LM step: sample-GFLOP/s (useful FLOP of both sweeps / step time)",
+                "value": round(r["value"], 1), "unit": "sample-GFLOP/s", "n_gpus": 1,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(r["ms_step"], 2),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "%s/f32-acc/f64-solve" % args.precision,
+                "data": "synthetic (seeded generator, on device)",
+                "config": {"workload": "batch32: 32 independent optimisations, n 500-8000, N_s "
+                                       "5e4-4e5 (%d samples in all), N_B 2-32 (blocks <= 640), "
+                                       "K <= 10, split tensor-core sweeps + FP64 solves, "
+                                       "autotuned tiles, one captured CUDA graph" % r["samples"],
+                           "input": "FP32 samples resident in HBM",
+                           "l2": "inputs larger than L2 (no flush needed)",
+                           "parallelism": "single GPU"},
+                "roofline": r["roofline"], "clocks": r["clocks"], "gpu_launches": r["gpu_launches"],
+                "phases_ms_per_step": {k: round(v[0], 2) for k, v in r["prof"].items() if v[1]},
+                "dominant_kernel": r["dominant"], "tile_choices": r["choices"],
+                "e_pred": r["e_pred"][:4], "e2e": None}
+        print(json.dumps(line))
+        return
     wl = synth.workload(args.workload)
     if args.samples:
         wl.n_samples = args.samples
-    config = {"workload": "%s: n=%d params, N_B=%d blocks, K=%d, N_s=%d samples in chunks of %d, %s"
-                          % (args.workload, wl.n, wl.n_blocks, wl.n_keep, wl.n_samples, wl.chunk,
-                             "split-BF16 tensor-core sweeps + FP64 solves" if args.precision == "bf16x4"
-                             else "FP64 sweeps + FP64 solves"),
-              "input": "FP32 samples resident in HBM" if args.precision == "bf16x4" else "FP64 samples resident in HBM",
+    path = {"bf16x4": "split-BF16 tensor-core sweeps + FP64 solves",
+            "tf32x4": "split-TF32 tensor-core sweeps + FP64 solves",
+            "f64": "FP64 sweeps + FP64 solves"}[args.precision]
+    blocks = ("%d blocks" % wl.n_blocks if len(set(np.diff(wl.block_offsets))) == 1 else
+              "%d uneven blocks of %d-%d" % (wl.n_blocks, min(np.diff(wl.block_offsets)),
+                                            max(np.diff(wl.block_offsets))))
+    config = {"workload": "%s: n=%d params, N_B=%s, K=%d, N_s=%d samples in chunks of %d, %s%s"
+                          % (args.workload, wl.n, blocks, wl.n_keep, wl.n_samples, wl.chunk, path,
+                             ", the whole step one captured CUDA graph" if args.graph else ""),
+              "input": ("FP32" if args.precision != "f64" else "FP64") + " samples resident in HBM",
               "l2": "inputs larger than L2 (no flush needed)",
               "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
     metric = "blocked-LM step: sample-GFLOP/s (useful FLOP of both sweeps / step time)"
@@ -533,7 +729,8 @@ def main():
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(res["ms_step"], 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16x4/f32-acc/f64-solve" if args.precision == "bf16x4" else "f64",
+            "dtype": {"bf16x4": "bf16x4/f32-acc/f64-solve", "tf32x4": "tf32x4/f32-acc/f64-solve",
+                      "f64": "f64"}[args.precision],
             "data": "synthetic (seeded generator, on device)", "config": config,
             "e_pred": res["e_pred"], "roofline": res["roofline"], "clocks": res["clocks"],
             "gpu_launches": res["gpu_launches"],
@@ -545,6 +742,8 @@ def main():
         line["fp64_path"] = res["fp64_path"]
     if "err_vs_fp64" in res:
         line["err_vs_fp64"] = res["err_vs_fp64"]
+    if "mixed_hist" in res:
+        line["mixed_hist"] = res["mixed_hist"]
     if not args.no_e2e and world == 1:
         line["e2e"] = run_e2e(args)
     else:

@@ -21,8 +21,10 @@
  *
  * Conventions
  *   - Sample arrays may be device memory or host memory (pinned or pageable); host arrays are
- *     copied through the handle's two staging buffers (256 MiB each, allocated on the
- *     handle's first host-memory call).  Element type per blm_problem.input_type.
+ *     copied in pieces of up to 32768 samples through the handle's two staging buffers
+ *     (allocated on the handle's first host-memory call), the copies on a stream of their own
+ *     overlapping the computation on the previous piece (see also blm_set_host_cache).
+ *     Element type per blm_problem.input_type.
  *   - All calls are asynchronous on the handle's stream; results are valid once it syncs.
  *   - The handle owns every accumulator and workspace it needs (allocated in blm_create; the
  *     host staging buffers on its first host-memory call).
@@ -61,8 +63,10 @@ typedef enum {
                           bf16 hi + lo (2^-16 relative), the four products hi*hi + hi*lo +
                           lo*hi + lo*lo accumulated in FP32 (TMEM), promoted to FP64;
                           centring and eigen-solves stay FP64                                */
-  BLM_PREC_TF32X3 = 2  /* as BF16X4 with a TF32 hi + FP32 lo split (2^-22 relative) and the
-                          three products hi*hi + hi*lo + lo*hi on kind::tf32                 */
+  BLM_PREC_TF32X4 = 2  /* the same four products on kind::tf32 with a finer lo: hi = the value
+                          rounded to 8 significant bits, lo = tf32(v - hi) (11 bits), so hi + lo
+                          represents v to 2^-21 (8x the BF16 split's resolution) at twice the
+                          tensor-core cost                                                      */
 } blm_precision;
 
 /* Element type of the sample arrays.  The tensor-core precisions take FP32 samples; the FP64
@@ -75,14 +79,19 @@ typedef struct {
   const int64_t* block_offsets;   /* host, n_blocks+1 increasing, [0] = 0, [N_B] = N_V;
                                      block b is parameters [off[b], off[b+1]) (contiguous)   */
   int32_t n_keep;                 /* N_K: directions kept per block (min(N_K, M_b) used)     */
-  int32_t n_old;                  /* N_O: previous-update directions (Eq. 9), 0 = none; 0..16,
-                                     N_O > 0 needs precision BLM_PREC_F64                    */
+  int32_t n_old;                  /* N_O: previous-update directions (Eq. 9), 0 = none; 0..16
+                                     (every precision: on the split paths their projections
+                                     and sums are tensor-core tiles of the first sweep)      */
   const double* old_dirs;         /* host or device, n_old x n_params row-major: row j is the
                                      overall update of iteration n-j (Sec. II.B); block k's
                                      slice of row j is D_jk.  Copied at blm_create.          */
   int32_t precision;              /* blm_precision                                           */
   int32_t input_type;             /* blm_input_type                                          */
   double shift;                   /* diagonal shift of Sec. II.A on the tangent space (>= 0) */
+  int64_t pass_samples;           /* samples per internal pass of a sweep (0 = 65536): the
+                                     operand and projection scratch are sized for it (split
+                                     precisions: 12 (BF16X4) or 24 (TF32X4) bytes per parameter
+                                     and sample); a multiple of 1024 in 1024 .. 2^20          */
 } blm_problem;
 
 typedef struct blm_handle blm_handle;
@@ -122,6 +131,69 @@ blm_status blm_project(blm_handle* h, const void* O, const void* dEL, const void
  * alpha ~ 0. */
 blm_status blm_combined_solve(blm_handle* h, double* dmu, double* e_pred);
 
+/* One whole step as a CUDA graph (Sec. II.B's step: both sweeps and both solves; the graph is
+ * an execution device with no counterpart in the paper).  blm_graph_capture records, on a
+ * stream of the handle's own, the step over the device sample arrays O, dEL (n_samples x ld),
+ * EL and w (NULL = unit weights) taken in chunks of `chunk` samples -- reset, blm_accumulate per
+ * chunk, blm_block_solve, blm_project per chunk, blm_combined_solve with Delta mu written to
+ * the device array dmu (n_params doubles) -- with no host synchronisation inside (statuses
+ * stay on the device; Davidson's dense fallback is decided on the device).  Nothing runs at
+ * capture.  blm_graph_launch enqueues the captured step on the handle's stream; it reads
+ * whatever the arrays hold at that time, so a sampler can refill the same buffers between
+ * launches.  blm_graph_result synchronises the stream and reports the launched step as the
+ * eager calls would (BLM_ERR_TIMEOUT, BLM_ERR_NUMERIC with blm_last_error) and its predicted
+ * energy; blm_get_block / blm_get_combined then read its matrices.  The graph and the eager
+ * calls share the handle's buffers: do not interleave them within a step.  All pointers must be
+ * device memory (BLM_ERR_ARG otherwise); a new capture replaces the previous graph. */
+blm_status blm_graph_capture(blm_handle* h, const void* O, const void* dEL, const void* EL,
+                             const void* w, int64_t n_samples, int64_t chunk, int64_t ld,
+                             double* dmu);
+blm_status blm_graph_launch(blm_handle* h);
+blm_status blm_graph_result(blm_handle* h, double* e_pred);
+
+/* Many independent optimisations in one graph (Sec. II.B: the block problems of a step are
+ * independent of one another, and so are separate optimisations; the batch is an execution
+ * device with no counterpart in the paper).  blm_batch_create makes one handle per problem
+ * (each as blm_create would; NULL on failure) bound to `stream`.  blm_batch_capture records one
+ * step of every problem, from the device arrays O[i], dEL[i], EL[i], w[i] (w or its entries may
+ * be NULL) of n_samples[i] rows with stride ld[i], taken in chunks of `chunk` samples, with
+ * Delta mu written to the device array dmu[i]: the problems' sweeps run on parallel branches of
+ * the graph, the block eigen-solves of all problems in one launch (one CTA per block problem
+ * across the whole batch), the dense combined solves of all problems in one launch, larger
+ * combined problems by Davidson one after another.  blm_batch_launch enqueues the graph on
+ * `stream`; blm_batch_result synchronises it and writes every problem's predicted energy
+ * (NaN where it failed) and, if status is not NULL, its blm_status; it returns BLM_OK if every
+ * problem succeeded, else the first failure (message in blm_batch_last_error).
+ * blm_batch_handle(b, i) is problem i's handle, for blm_get_block / blm_get_combined (do not
+ * destroy it); blm_batch_destroy frees everything. */
+typedef struct blm_batch blm_batch;
+blm_status blm_batch_create(const blm_problem* problems, int32_t count, void* stream,
+                            blm_batch** out);
+blm_status blm_batch_capture(blm_batch* b, const void* const* O, const void* const* dEL,
+                             const void* const* EL, const void* const* w,
+                             const int64_t* n_samples, const int64_t* ld, int64_t chunk,
+                             double* const* dmu);
+blm_status blm_batch_launch(blm_batch* b);
+blm_status blm_batch_result(blm_batch* b, double* e_pred, int32_t* status);
+blm_handle* blm_batch_handle(blm_batch* b, int32_t i);
+const char* blm_batch_last_error(const blm_batch* b);
+blm_status blm_batch_destroy(blm_batch* b);
+
+/* Tile autotuner for the split-precision sweeps (no counterpart in the paper).  Times the first
+ * sweep's preparation and tensor-core contraction on the given device FP32 samples (at most one
+ * pass, see blm_problem.pass_samples) for each candidate -- tile layout (one set of 128 x 256
+ * tiles per block, or 128-row band tiles across the parameter range that keep only products
+ * within a block, better for blocks much smaller than a tile) x the longest work unit (16384 or
+ * 4096 samples) -- keeps the fastest for the handle and clears the sums (the step starts
+ * afresh).  *choice (may be NULL) = 2 layout + unit index.  Synchronises the stream; no-op
+ * (choice 0) on the FP64 path.  Results do not depend on the choice beyond the rounding of the
+ * sums' accumulation order. */
+blm_status blm_autotune(blm_handle* h, const void* O, const void* dEL, const void* EL,
+                        const void* w, int64_t n_samples, int64_t ld, int32_t* choice);
+/* Sets a candidate of blm_autotune directly (0 .. 3, e.g. one recorded from an earlier tuning);
+ * takes effect from the next sweep.  Synchronises the stream; no-op on the FP64 path. */
+blm_status blm_set_tiles(blm_handle* h, int32_t choice);
+
 /* Read back block b's matrices (host, row-major (1+d_b)^2 with d_b = M_b + N_O (N_B - 1)),
  * its kept eigenvalues (host, min(N_K,M_b)) and B^(b) (host, min(N_K,M_b) x M_b).  Any output
  * pointer may be NULL.  Valid after blm_block_solve; synchronises the stream. */
@@ -143,6 +215,26 @@ blm_status blm_destroy(blm_handle* h);
 
 /* Last error message of the handle ("" if none); valid until the next call on it. */
 const char* blm_last_error(const blm_handle* h);
+
+/* Second sweep without a second host-to-device copy (Sec. II.B: the second sweep re-runs the
+ * same samples).  Reserves `bytes` of device memory (0 releases it) in which blm_accumulate
+ * keeps its device copies of host sample arrays, piece by piece while room remains; blm_project
+ * given the same host arrays (same addresses, same chunking) then reads the kept copies instead
+ * of copying the samples again.  Pieces that do not fit are copied in both sweeps as before.
+ * blm_reset forgets the kept copies.  Synchronises the handle's stream; BLM_ERR_NOMEM if the
+ * reservation fails.  Device sample arrays are never copied, with or without a cache. */
+blm_status blm_set_host_cache(blm_handle* h, size_t bytes);
+
+/* Failure detection (no counterpart in the paper).  Every wait of a tensor-core kernel on its
+ * pipeline (operand stages, accumulator drains) polls an mbarrier at most `polls` times; then
+ * the kernel records a timeout, waits for the copies and tensor-core operations it already
+ * issued (those always complete), frees its tensor memory and returns, and the next solve on
+ * the handle returns BLM_ERR_TIMEOUT (blm_reset clears it).  A handle starts with
+ * BLM_WAIT_LIMIT_DEFAULT, far beyond any healthy wait.  polls = 0 makes every pipeline wait give
+ * up at once: a deterministic way to run the timeout path, to test that the handle and the CUDA
+ * context stay usable after it. */
+#define BLM_WAIT_LIMIT_DEFAULT (1u << 24)
+blm_status blm_set_wait_limit(blm_handle* h, uint32_t polls);
 
 /* Profiling (no counterpart in the paper: measurement support).  While enabled, the handle
  * records a pair of CUDA events on its stream around each kernel it launches and counts the
@@ -166,7 +258,7 @@ const char* blm_profile_class_name(int i);
  * (device, n_keep) and the corresponding directions into B (device, n_keep x (dim - 1),
  * unit 2-norm, largest-magnitude entry positive), exactly as blm_get_block reports them.
  *
- * Workspace: a static device array inside the library (about 7.2 MB, held by every GPU that
+ * Workspace: a static device array inside the library (about 11.6 MB, held by every GPU that
  * loads the library until the process exits); nothing is allocated or freed.  Limits: 2 <= dim
  * <= blm_noalloc_max_dim() (257), 1 <= n_keep <= min(64, dim - 1); larger sizes return
  * BLM_ERR_ARG with a message on stderr.  The first call on each device looks up the array's

@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(_HERE, "libblm.so")
 
 BLM_OK, BLM_ERR_ARG, BLM_ERR_STATE, BLM_ERR_NUMERIC, BLM_ERR_NOMEM, BLM_ERR_CUDA, \
     BLM_ERR_TIMEOUT, BLM_ERR_UNSUPPORTED = range(8)
-BLM_PREC_F64, BLM_PREC_BF16X4, BLM_PREC_TF32X3 = 0, 1, 2
+BLM_PREC_F64, BLM_PREC_BF16X4, BLM_PREC_TF32X4 = 0, 1, 2
 BLM_IN_F64, BLM_IN_F32 = 0, 1
 STATUS_NAMES = {0: "BLM_OK", 1: "BLM_ERR_ARG", 2: "BLM_ERR_STATE", 3: "BLM_ERR_NUMERIC",
                 4: "BLM_ERR_NOMEM", 5: "BLM_ERR_CUDA", 6: "BLM_ERR_TIMEOUT", 7: "BLM_ERR_UNSUPPORTED"}
@@ -35,7 +35,8 @@ class blm_problem(ctypes.Structure):
                 ("old_dirs", ctypes.c_void_p),
                 ("precision", ctypes.c_int32),
                 ("input_type", ctypes.c_int32),
-                ("shift", ctypes.c_double)]
+                ("shift", ctypes.c_double),
+                ("pass_samples", ctypes.c_int64)]
 
 
 _H = ctypes.c_void_p
@@ -53,6 +54,24 @@ _sig = {
     "blm_reset": (ctypes.c_int, [_H]),
     "blm_destroy": (ctypes.c_int, [_H]),
     "blm_last_error": (ctypes.c_char_p, [_H]),
+    "blm_set_wait_limit": (ctypes.c_int, [_H, ctypes.c_uint32]),
+    "blm_set_host_cache": (ctypes.c_int, [_H, ctypes.c_size_t]),
+    "blm_graph_capture": (ctypes.c_int, [_H, _P, _P, _P, _P, ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.c_int64, _P]),
+    "blm_graph_launch": (ctypes.c_int, [_H]),
+    "blm_autotune": (ctypes.c_int, [_H, _P, _P, _P, _P, ctypes.c_int64, ctypes.c_int64,
+                                    ctypes.POINTER(ctypes.c_int32)]),
+    "blm_set_tiles": (ctypes.c_int, [_H, ctypes.c_int32]),
+    "blm_batch_create": (ctypes.c_int, [ctypes.POINTER(blm_problem), ctypes.c_int32,
+                                        ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "blm_batch_capture": (ctypes.c_int, [ctypes.c_void_p, _P, _P, _P, _P, _P, _P,
+                                         ctypes.c_int64, _P]),
+    "blm_batch_launch": (ctypes.c_int, [ctypes.c_void_p]),
+    "blm_batch_result": (ctypes.c_int, [ctypes.c_void_p, _P, _P]),
+    "blm_batch_handle": (ctypes.c_void_p, [ctypes.c_void_p, ctypes.c_int32]),
+    "blm_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "blm_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "blm_graph_result": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_double)]),
     "blm_memory_estimate": (ctypes.c_size_t, [ctypes.POINTER(blm_problem)]),
     "blm_lm_matrix_bytes": (ctypes.c_double, [ctypes.c_int64]),
     "blm_matrix_bytes_dominant": (ctypes.c_double, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32]),
@@ -89,10 +108,11 @@ def _ptr(x):
 
 
 def make_problem(n_params, block_offsets, n_keep, n_old=0, old_dirs=None,
-                 precision=BLM_PREC_F64, input_type=BLM_IN_F64, shift=0.0):
+                 precision=BLM_PREC_F64, input_type=BLM_IN_F64, shift=0.0, pass_samples=0):
     offs = (ctypes.c_int64 * len(block_offsets))(*[int(o) for o in block_offsets])
     p = blm_problem(int(n_params), len(block_offsets) - 1, offs, int(n_keep), int(n_old),
-                    _ptr(old_dirs), int(precision), int(input_type), float(shift))
+                    _ptr(old_dirs), int(precision), int(input_type), float(shift),
+                    int(pass_samples))
     p._keep = (offs, old_dirs)          # keep the arrays alive with the struct
     return p
 
@@ -159,6 +179,93 @@ def blm_last_error(h):
     return _lib.blm_last_error(h).decode()
 
 
+def blm_set_host_cache(h, nbytes):
+    _check(h, _lib.blm_set_host_cache(h, int(nbytes)), "blm_set_host_cache")
+
+
+BLM_WAIT_LIMIT_DEFAULT = 1 << 24
+
+
+def blm_set_wait_limit(h, polls):
+    _check(h, _lib.blm_set_wait_limit(h, int(polls)), "blm_set_wait_limit")
+
+
+def blm_graph_capture(h, O, dEL, EL, w, n_samples, chunk, ld, dmu):
+    _check(h, _lib.blm_graph_capture(h, _ptr(O), _ptr(dEL), _ptr(EL), _ptr(w), int(n_samples),
+                                     int(chunk), int(ld), _ptr(dmu)), "blm_graph_capture")
+
+
+def blm_autotune(h, O, dEL, EL, w, n_samples, ld):
+    """Chooses the tile layout and work-unit length for the handle; returns the choice index."""
+    c = ctypes.c_int32()
+    _check(h, _lib.blm_autotune(h, _ptr(O), _ptr(dEL), _ptr(EL), _ptr(w), int(n_samples), int(ld),
+                                ctypes.byref(c)), "blm_autotune")
+    return c.value
+
+
+def blm_set_tiles(h, choice):
+    _check(h, _lib.blm_set_tiles(h, int(choice)), "blm_set_tiles")
+
+
+def blm_graph_launch(h):
+    _check(h, _lib.blm_graph_launch(h), "blm_graph_launch")
+
+
+def blm_graph_result(h):
+    e = ctypes.c_double()
+    _check(h, _lib.blm_graph_result(h, ctypes.byref(e)), "blm_graph_result")
+    return e.value
+
+
+def _bcheck(b, st, what):
+    if st != BLM_OK:
+        raise BLMError(st, "%s: %s" % (what, _lib.blm_batch_last_error(b).decode()))
+
+
+def blm_batch_create(problems, stream=0):
+    arr = (blm_problem * len(problems))(*problems)
+    b = ctypes.c_void_p()
+    st = _lib.blm_batch_create(arr, len(problems), ctypes.c_void_p(int(stream)), ctypes.byref(b))
+    if st != BLM_OK:
+        raise BLMError(st, "blm_batch_create failed")
+    return b
+
+
+def _ptr_array(xs):
+    return (ctypes.c_void_p * len(xs))(*[None if x is None else _ptr(x).value for x in xs])
+
+
+def blm_batch_capture(b, O, dEL, EL, w, n_samples, ld, chunk, dmu):
+    """Lists of per-problem device arrays (w may be None or a list with None entries)."""
+    k = len(O)
+    ns = (ctypes.c_int64 * k)(*[int(x) for x in n_samples])
+    lds = (ctypes.c_int64 * k)(*[int(x) for x in ld])
+    wp = None if w is None else _ptr_array(w)
+    _bcheck(b, _lib.blm_batch_capture(b, _ptr_array(O), _ptr_array(dEL), _ptr_array(EL), wp, ns,
+                                      lds, int(chunk), _ptr_array(dmu)), "blm_batch_capture")
+
+
+def blm_batch_launch(b):
+    _bcheck(b, _lib.blm_batch_launch(b), "blm_batch_launch")
+
+
+def blm_batch_result(b, count):
+    """(predicted energies, statuses) of the last launch; raises on the first failure."""
+    import numpy as np
+    e = np.empty(count)
+    st = np.empty(count, dtype=np.int32)
+    r = _lib.blm_batch_result(b, _ptr(e), _ptr(st))
+    return e, st, r
+
+
+def blm_batch_handle(b, i):
+    return _H(_lib.blm_batch_handle(b, int(i)))
+
+
+def blm_batch_destroy(b):
+    _lib.blm_batch_destroy(b)
+
+
 def blm_memory_estimate(problem):
     return int(_lib.blm_memory_estimate(ctypes.byref(problem)))
 
@@ -201,9 +308,10 @@ class Step:
     problem's input dtype, on the device or on the host."""
 
     def __init__(self, n_params, block_offsets, n_keep, n_old=0, old_dirs=None,
-                 precision=BLM_PREC_F64, input_type=BLM_IN_F64, shift=0.0, stream=0):
+                 precision=BLM_PREC_F64, input_type=BLM_IN_F64, shift=0.0, stream=0,
+                 pass_samples=0):
         self.problem = make_problem(n_params, block_offsets, n_keep, n_old, old_dirs, precision,
-                                    input_type, shift)
+                                    input_type, shift, pass_samples)
         self.n = int(n_params)
         self.offsets = [int(o) for o in block_offsets]
         self.n_keep = int(n_keep)

@@ -916,7 +916,7 @@ __device__ bool hqr_windowed(R* G, int m, double* wr, double* wi, double anorm, 
 // with the factors.  Rows being eliminated live in shared memory (cur, nxt); U is stored packed
 // (row k holds columns k..m-1).  CX selects complex arithmetic (complex shift) at compile time.
 // ---------------------------------------------------------------------------------------------
-constexpr int kVecWarps = 8;                           // warps running inverse iteration
+constexpr int kVecWarps = 16;                          // warps running inverse iteration
 constexpr int kEigSmemDoubles = 200 * 1024 / 8;        // dynamic shared memory of the solver
 static_assert(kQrSmemDoubles <= kEigSmemDoubles, "QR window exceeds the solver's shared memory");
 
@@ -1739,7 +1739,9 @@ __global__ void __launch_bounds__(kEigThreads)
 eig_kernel(const EigProblem* __restrict__ probs) {
   extern __shared__ double dsm[];
   __shared__ Shared sh;
-  dense_geig(probs[blockIdx.x], dsm, sh);
+  const EigProblem pb = probs[blockIdx.x];
+  if (pb.run_if_noconv && *pb.run_if_noconv != ST_NOCONV) return;
+  dense_geig(pb, dsm, sh);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -2082,9 +2084,8 @@ size_t davidson_work_doubles(int64_t m) {
                   sizeof(DavCtl) / 8 + 8);
 }
 
-void launch_davidson(const EigProblem* probs, int nprob, double tol, int max_iter,
-                     cudaStream_t st) {
-  (void)nprob;   // one problem (the combined one), spread over every SM
+cudaError_t launch_davidson(const EigProblem* probs, double tol, int max_iter, double* work, int m,
+                            cudaStream_t st) {
   static int grid = 0;
   const int smem = 200 * 1024;
   if (grid == 0) {
@@ -2096,15 +2097,22 @@ void launch_davidson(const EigProblem* probs, int nprob, double tol, int max_ite
     grid = sms * (per_sm > 0 ? per_sm : 1);
   }
   // the control block sits at the end of the problem's workspace
-  EigProblem pb;
-  cudaMemcpyAsync(&pb, probs, sizeof(pb), cudaMemcpyDeviceToHost, st);
-  cudaStreamSynchronize(st);
-  DavCtl* ctl = reinterpret_cast<DavCtl*>(pb.work + davidson_work_doubles(pb.m) -
-                                          sizeof(DavCtl) / 8 - 4);
-  cudaMemsetAsync(ctl, 0, sizeof(DavCtl), st);
-  void* args[] = {(void*)&probs, (void*)&tol, (void*)&max_iter, (void*)&ctl};
-  cudaLaunchCooperativeKernel((const void*)davidson_kernel, dim3(grid), dim3(kEigThreads), args,
-                              smem, st);
+  DavCtl* ctl = reinterpret_cast<DavCtl*>(work + davidson_work_doubles(m) - sizeof(DavCtl) / 8 - 4);
+  cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(DavCtl), st);
+  if (e != cudaSuccess) return e;
+  // a cooperative launch (every CTA resident: the grid barriers need it), written with the
+  // launch-attribute form so that it can also be captured into a CUDA graph
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kEigThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, davidson_kernel, probs, tol, max_iter, ctl);
 }
 
 void launch_eig(const EigProblem* probs, int nprob, int threads, cudaStream_t st) {

@@ -95,40 +95,61 @@ void launch_project(const T* O, const T* G, int64_t ldo, int64_t ldg, const doub
                     const float* shift32,
                     const ProjBlock* blocks, int nblocks, const double* cen, TO* Y, TO* Z,
                     int64_t ldout, int64_t ns, int max_m, int max_nd, cudaStream_t st);
-// Split-BF16 operands of a chunk of at most row_bytes / 4 samples (blm_prep.cu): rows of
-// row_bytes per parameter, 128 bytes per 32-sample group ([hi(32) | lo(32)] bf16).  opBS is
-// written only when w is given.  With sY non-null the same pass adds the first moments
-// sum w Y', sum w E Y', sum w Z into sY, sEY, sZ (and sum w, sum w E into scal if non-null).
+// Split operands of a chunk (blm_prep.cu): rows of row_bytes per parameter, 128 bytes per
+// sample group -- BF16 (tf32 = 0): 32 samples [hi(32) | lo(32)] bf16, a chunk of at most
+// row_bytes / 4 samples; TF32 (tf32 = 1): 16 samples [hi(16) | lo(16)] tf32, at most
+// row_bytes / 8 samples.  opBS is written only when w is given.  With sY non-null the same pass
+// adds the first moments sum w Y', sum w E Y', sum w Z into sY, sEY, sZ (and sum w, sum w E into
+// scal if non-null).
 void launch_prep(const float* Y, const float* Z, const float* E, const float* w, int64_t ns,
                  int64_t ld, int64_t n, const float* shift32, uint8_t* opA, uint8_t* opBS,
                  uint8_t* opBH, int64_t row_bytes, double* sY, double* sEY, double* sZ,
-                 double* scal, cudaStream_t st);
+                 double* scal, int tf32, cudaStream_t st);
 // dst[i] = (float)src[i], i < count
 void launch_to_f32(const double* src, float* dst, int64_t count, cudaStream_t st);
 
 // ------------------------------- launchers (blm_sweep_tc.cu) ---------------------------------
-// Split-BF16 tcgen05 accumulation: for each tile, rows [row0, row0 + 128) and columns
-// [col0, col0 + 256) of C_b = sum_s w_s Y'_b [Y'_b | E Y'_b + Z_b]^T  (Y' = Y - shift; the block
-// is columns [lo, lo + m) of Y and Z; out is C_b, m x 2m row-major FP64, accumulated into).
+// One 128 x 256 output tile of a split-precision tcgen05 contraction (blm_sweep_tc.cu):
+//   out[r * out_ld + c] += sum_s A(s, r) B(s, c),   r < nA (<= 128), c < nB (<= 256),
+// where A is operand rows a_row .. a_row + 127 of prepared operand array a_map and B rows
+// b_row .. b_row + 255 of array b_map (prepared rows: one per parameter or direction, see
+// launch_prep).  a_view: A's rows lie inside the B rows of the same stage (a_map and b_map hold
+// the same data when the sums are unweighted), so A needs no load of its own.
 struct TcTile {
-  int64_t lo;
-  int32_t m;
-  int32_t row0;
-  int32_t col0;
-  int32_t pad;
+  int32_t a_map, b_map;
+  int32_t a_row, b_row;
+  int32_t nA, nB;
+  int32_t a_view;      // 1: A is rows [a_row - b_row, a_row - b_row + 128) of the B stage when
+                       //    the launch is unweighted
+  int32_t packed;      // 1: a band tile over several blocks (TcPack): out and out_ld unused,
+                       //    each product lands in its block's sums if row and column share a
+                       //    block (b_map 2: the Hamiltonian half of the block's sums)
   double* out;
+  int64_t out_ld;
 };
-// Tensor-core contraction of prepared operands (blm_sweep_tc.cu, tc_op_kernel).
-cudaError_t launch_tc_prepared(const uint8_t* opA, const uint8_t* opBS, const uint8_t* opBH,
-                               int64_t nrows, int64_t row_bytes, int64_t ns, const TcTile* tiles,
-                               int ntiles, int weighted, int32_t* err, cudaStream_t st);
-bool tc_supported();
-// Tensor-core contraction of one chunk from FP32 rows converted in the kernel (blm_sweep_tc.cu,
-// tc_accumulate_kernel; the TF32X3 path).
-cudaError_t launch_tc_accumulate(const float* Y, const float* Z, const float* E, const float* w,
-                                 int64_t ns, int64_t ncols, int64_t ld, const float* shift32,
-                                 const TcTile* tiles, int ntiles, int32_t* err, int tf32,
-                                 cudaStream_t st);
+// Block tables of packed tiles: block of each parameter, first parameter, size and sums
+// (M_b x 2 M_b) of each block.
+struct TcPack {
+  const int32_t* blk_of;
+  const int64_t* lo;
+  const int32_t* m;
+  double* const* C;
+};
+// Operand arrays of one tensor-core launch (up to kTcMaps prepared arrays, rows x row_bytes).
+constexpr int kTcMaps = 6;
+struct TcOperands {
+  const uint8_t* op[kTcMaps];
+  int64_t rows[kTcMaps];
+};
+// Tensor-core contraction of prepared operands (blm_sweep_tc.cu, tc_op_kernel); tf32 selects
+// the TF32 split (operands prepared with launch_prep(..., tf32 = 1)).
+// wait_limit: polls of a pipeline wait before the kernel gives up and records a timeout in *err
+// (BLM_WAIT_LIMIT_DEFAULT normally; 0 gives up at the first wait).
+// max_range: longest sample range of a work unit (a multiple of 2048, tuned per problem).
+cudaError_t launch_tc_prepared(const TcOperands& ops, int64_t row_bytes, int64_t ns,
+                               const TcTile* tiles, int ntiles, int weighted, int32_t* err,
+                               uint32_t wait_limit, int tf32, const TcPack& pack,
+                               int64_t max_range, cudaStream_t st);
 
 // ------------------------------- launchers (blm_assemble.cu) ---------------------------------
 struct BlockAsm {
@@ -141,7 +162,7 @@ struct BlockAsm {
   double* S;           // (1+d)^2 output
   double* H;           // (1+d)^2 output
 };
-struct HistSums {      // history sums (N_O > 0), R = N_O * N_B virtual columns t_jk, r = j*N_B+k
+struct HistSums {      // history sums (N_O > 0), R = N_O * N_B virtual columns t_jk, r = k*N_O+j
   int32_t n_old, n_blocks;
   const double* OT;    // n x 2R: [sum w O' T' | sum w O' (E T' + U)]
   const double* XT;    // n x R : sum w X' T'
@@ -170,12 +191,16 @@ struct EigProblem {
   double* lam;         // k outputs (real parts)
   double* vec;         // k x m outputs (real eigenvectors in the original basis)
   int32_t* status;     // one word
+  const int32_t* run_if_noconv;  // if set: solve only when *run_if_noconv == ST_NOCONV (the
+                                 // dense fallback after a Davidson run, decided on the device)
 };
 void launch_eig(const EigProblem* probs, int nprob, int threads, cudaStream_t st);
 size_t eig_work_doubles(int64_t m);
-// Lowest eigenpair by generalized Davidson (k = 1, mode 1); work: davidson_work_doubles(m).
-void launch_davidson(const EigProblem* probs, int nprob, double tol, int max_iter,
-                     cudaStream_t st);
+// Lowest eigenpair by generalized Davidson (k = 1, mode 1) of the one problem *probs, whose
+// workspace `work` (device, davidson_work_doubles(m) doubles) and dimension m the caller passes
+// (no read-back: the launch is stream-ordered and can be captured in a graph).
+cudaError_t launch_davidson(const EigProblem* probs, double tol, int max_iter, double* work, int m,
+                            cudaStream_t st);
 size_t davidson_work_doubles(int64_t m);
 
 // ------------------------------- launchers (blm_update.cu) -----------------------------------

@@ -1,9 +1,10 @@
-// Operand preparation for the split-BF16 sweeps (Eq. 3 / Eq. 5 / Eq. 7 sums on tensor cores),
-// fused with the first-moment sums of the same sweep.
+// Operand preparation for the split-precision sweeps (Eq. 3 / Eq. 5 / Eq. 7 sums on tensor
+// cores), fused with the first-moment sums of the same sweep.
 //
 // Each FP32 sample element is converted once per sweep into the operands of the tensor-core
 // contraction, stored in HBM in the layout the tensor core reads (K-major, one 128-byte row per
-// parameter and 32-sample group: [hi(32 samples) | lo(32 samples)] in bf16):
+// parameter and sample group: [hi(32 samples) | lo(32 samples)] in bf16, or [hi(16) | lo(16)]
+// in TF32):
 //   opA  = Y' = Y - c                       (A operand, all tiles)
 //   opBH = w (E Y' + Z)                     (B operand of the Hamiltonian tiles, X')
 //   opBS = w Y'                             (B operand of the overlap tiles when weighted;
@@ -56,6 +57,48 @@ __device__ __forceinline__ void split8_bf16(const float* v, uint4& hi, uint4& lo
   lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
+// hi/lo split of 4 values for the TF32 products: hi = v rounded to 8 significant bits (a bf16
+// value, exact in TF32), lo = tf32(v - hi) (11 bits, round to nearest); both have their low 13
+// bits zero, so the tensor core reads them exactly, and hi + lo represents v to 2^-21.  hi keeps
+// as few bits as the BF16 split's so that the hi*hi products (16 significant bits) lose as
+// little to the accumulator's truncation as there.
+__device__ __forceinline__ void split4_tf32(const float* v, uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t hb = pack_bf16x2(v[k], 0.0f);          // bf16(v) in the low half
+    h[k] = hb << 16;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l[k]) : "f"(v[k] - __uint_as_float(h[k])));
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Writes one thread's 8 consecutive samples (tile-relative sample 8 sb, tile start s0t) of one
+// parameter row: BF16 rows hold 32-sample groups [hi(32) | lo(32)] of 2 bytes, TF32 rows
+// 16-sample groups [hi(16) | lo(16)] of 4 bytes; both are 128 bytes per group.
+template <bool TF>
+__device__ __forceinline__ void store_split8(uint8_t* row, int64_t s0t, int sb, const float* v) {
+  if (TF) {
+    const int64_t grp = s0t / 16 + (sb >> 1);
+    uint8_t* base = row + grp * 128 + 32 * (sb & 1);
+    uint4 hi, lo;
+    split4_tf32(v, hi, lo);
+    *reinterpret_cast<uint4*>(base) = hi;
+    *reinterpret_cast<uint4*>(base + 64) = lo;
+    split4_tf32(v + 4, hi, lo);
+    *reinterpret_cast<uint4*>(base + 16) = hi;
+    *reinterpret_cast<uint4*>(base + 80) = lo;
+  } else {
+    const int64_t grp = s0t / 32 + (sb >> 2);
+    uint8_t* base = row + grp * 128 + 16 * (sb & 3);
+    uint4 hi, lo;
+    split8_bf16(v, hi, lo);
+    *reinterpret_cast<uint4*>(base) = hi;
+    *reinterpret_cast<uint4*>(base + 64) = lo;
+  }
+}
+
 __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
                    (unsigned)__cvta_generic_to_shared(dst)),
@@ -87,6 +130,7 @@ struct PrepArgs {
   int vec;                // 16-byte copies allowed
 };
 
+template <bool TF>
 __global__ void __launch_bounds__(kPrepThreads)
 prep_kernel(const PrepArgs a) {
   extern __shared__ __align__(16) float sm[];
@@ -184,25 +228,13 @@ prep_kernel(const PrepArgs a) {
         fZ[e] = fmaf(wv, gv[e], fZ[e]);
       }
     }
-    const int64_t grp = s0 / 32 + (sb >> 2);
-    const int chunk = sb & 3;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int64_t p = p0 + 4 * p4 + e;
       if (p >= a.n) continue;
-      const int64_t off = p * a.row_bytes + grp * 128 + 16 * chunk;
-      uint4 hi, lo;
-      split8_bf16(ya[e], hi, lo);
-      *reinterpret_cast<uint4*>(a.opA + off) = hi;
-      *reinterpret_cast<uint4*>(a.opA + off + 64) = lo;
-      split8_bf16(xb[e], hi, lo);
-      *reinterpret_cast<uint4*>(a.opBH + off) = hi;
-      *reinterpret_cast<uint4*>(a.opBH + off + 64) = lo;
-      if (a.opBS) {
-        split8_bf16(yb[e], hi, lo);
-        *reinterpret_cast<uint4*>(a.opBS + off) = hi;
-        *reinterpret_cast<uint4*>(a.opBS + off + 64) = lo;
-      }
+      store_split8<TF>(a.opA + p * a.row_bytes, s0, sb, ya[e]);
+      store_split8<TF>(a.opBH + p * a.row_bytes, s0, sb, xb[e]);
+      if (a.opBS) store_split8<TF>(a.opBS + p * a.row_bytes, s0, sb, yb[e]);
     }
     if ((ti + 1) % kPrepRun == 0 || ti + 1 == ntiles) {
 #pragma unroll
@@ -264,7 +296,7 @@ prep_kernel(const PrepArgs a) {
 // ---------------------------------------------------------------------------------------------
 constexpr int kPdThreads = 128;
 
-template <bool WT>
+template <bool WT, bool TF>
 __global__ void __launch_bounds__(kPdThreads, 4)
 prep_direct_kernel(const PrepArgs a) {
   __shared__ double dsum[kPdThreads * 12];   // per thread: sY[4], sEY[4], sZ[4]; then reduction
@@ -327,24 +359,12 @@ prep_direct_kernel(const PrepArgs a) {
       }
     }
     const int64_t s0t = sbase + (int64_t)ti * kPrepT;
-    const int64_t grp = s0t / 32 + (sb >> 2);
-    const int chunk = sb & 3;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       if (e >= nval) continue;
-      const int64_t off = (pq + e) * a.row_bytes + grp * 128 + 16 * chunk;
-      uint4 hi, lo;
-      split8_bf16(ya[e], hi, lo);
-      *reinterpret_cast<uint4*>(a.opA + off) = hi;
-      *reinterpret_cast<uint4*>(a.opA + off + 64) = lo;
-      split8_bf16(xb[e], hi, lo);
-      *reinterpret_cast<uint4*>(a.opBH + off) = hi;
-      *reinterpret_cast<uint4*>(a.opBH + off + 64) = lo;
-      if (WT) {
-        split8_bf16(yb[WT ? e : 0], hi, lo);
-        *reinterpret_cast<uint4*>(a.opBS + off) = hi;
-        *reinterpret_cast<uint4*>(a.opBS + off + 64) = lo;
-      }
+      store_split8<TF>(a.opA + (pq + e) * a.row_bytes, s0t, sb, ya[e]);
+      store_split8<TF>(a.opBH + (pq + e) * a.row_bytes, s0t, sb, xb[e]);
+      if (WT) store_split8<TF>(a.opBS + (pq + e) * a.row_bytes, s0t, sb, yb[WT ? e : 0]);
     }
     if ((ti + 1) % kPrepRun == 0 || ti + 1 == ntiles) {
 #pragma unroll
@@ -387,11 +407,12 @@ prep_direct_kernel(const PrepArgs a) {
 void launch_prep(const float* Y, const float* Z, const float* E, const float* w, int64_t ns,
                  int64_t ld, int64_t n, const float* shift32, uint8_t* opA, uint8_t* opBS,
                  uint8_t* opBH, int64_t row_bytes, double* sY, double* sEY, double* sZ,
-                 double* scal, cudaStream_t st) {
+                 double* scal, int tf32, cudaStream_t st) {
   if (ns <= 0) return;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPrepSmem);
+    cudaFuncSetAttribute(prep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPrepSmem);
+    cudaFuncSetAttribute(prep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPrepSmem);
     attr = true;
   }
   PrepArgs a{Y, Z, E, w, ns, ld, n, shift32, opA, w ? opBS : nullptr, opBH, row_bytes,
@@ -399,12 +420,21 @@ void launch_prep(const float* Y, const float* Z, const float* E, const float* w,
              (ld % 4 == 0) && ((((uintptr_t)Y) | ((uintptr_t)Z)) % 16 == 0) ? 1 : 0};
   dim3 grid((unsigned)((n + kPrepP - 1) / kPrepP),
             (unsigned)((ns + kPrepT * kPrepTiles - 1) / (kPrepT * kPrepTiles)));
-  if (a.vec && w)
-    prep_direct_kernel<true><<<grid, kPdThreads, 0, st>>>(a);
-  else if (a.vec)
-    prep_direct_kernel<false><<<grid, kPdThreads, 0, st>>>(a);
-  else
-    prep_kernel<<<grid, kPrepThreads, kPrepSmem, st>>>(a);
+  if (tf32) {
+    if (a.vec && w)
+      prep_direct_kernel<true, true><<<grid, kPdThreads, 0, st>>>(a);
+    else if (a.vec)
+      prep_direct_kernel<false, true><<<grid, kPdThreads, 0, st>>>(a);
+    else
+      prep_kernel<true><<<grid, kPrepThreads, kPrepSmem, st>>>(a);
+  } else {
+    if (a.vec && w)
+      prep_direct_kernel<true, false><<<grid, kPdThreads, 0, st>>>(a);
+    else if (a.vec)
+      prep_direct_kernel<false, false><<<grid, kPdThreads, 0, st>>>(a);
+    else
+      prep_kernel<false><<<grid, kPrepThreads, kPrepSmem, st>>>(a);
+  }
 }
 
 }  // namespace blm

@@ -95,6 +95,33 @@ def workload(name):
     raise KeyError(name)
 
 
+TAG_BATCH_N = 20
+TAG_BATCH_NS = 21
+TAG_BATCH_NB = 22
+
+
+def batch_workloads(count=32, seed=0, max_block=640):
+    """The batch of independent optimisations: for optimisation i (opt = i + 1, its own draws),
+    n ~ U{500..8000}, N_s ~ U{50000..400000} rounded to a multiple of 256, N_B ~ U{2..32} raised
+    to ceil(n / max_block) so that no block exceeds max_block parameters, near-equal contiguous
+    blocks, K = min(10, smallest block), normal local-energy noise."""
+    idx = np.arange(count, dtype=np.uint64)
+    un = philox.uniform(seed, 0, TAG_BATCH_N, idx)
+    us = philox.uniform(seed, 0, TAG_BATCH_NS, idx)
+    ub = philox.uniform(seed, 0, TAG_BATCH_NB, idx)
+    out = []
+    for i in range(count):
+        n = int(500 + np.floor(un[i] * 7501))
+        ns = int(np.round((50000 + np.floor(us[i] * 350001)) / 256.0) * 256)
+        nb = int(2 + np.floor(ub[i] * 31))
+        nb = max(nb, -(-n // max_block))
+        offs = equal_blocks(n, nb)
+        k = min(10, min(np.diff(offs)))
+        out.append(Workload("batch%d" % i, n, ns, offs, int(k), decades=6.0, chunk=65536,
+                            seed=seed, opt=i + 1))
+    return out
+
+
 @dataclass
 class Model:
     """The fixed (sample-independent) random draws of one optimisation."""

@@ -2,6 +2,23 @@
 import numpy as np
 
 
+def mixed_tolerances(n_samples):
+    """Tolerances of the split-precision path at a sample count N, from its stated targets at
+    the full step (10^6 samples: 1e-6 on S_b, H_b and the combined matrices in correlation
+    scaling, 1e-8 Hartree on E_pred).
+
+    Two error sources, measured at the full 16384-parameter shape for N = 16384 .. 10^6 (the
+    error scan recorded under profiles/): a systematic one, the truncating FP32 accumulation of
+    the tensor cores (a relative -3.3e-8 on the overlap diagonal, the same at every N), and a
+    zero-mean one, the residual of the hi + lo operand split (2^-17 per operand), whose effect
+    on a sum over N samples falls as 1/sqrt(N).  The systematic share of each target is held at
+    every N; only the zero-mean share is widened by sqrt(10^6 / N):
+        matrices  1e-7 + 9e-7 sqrt(10^6/N)     E_pred  3e-9 + 7e-9 sqrt(10^6/N) Hartree
+    (at N = 10^6 these are the targets themselves)."""
+    g = max(1.0, np.sqrt(1.0e6 / float(n_samples)))
+    return 1e-7 + 9e-7 * g, 3e-9 + 7e-9 * g
+
+
 def matrix_err(S_got, S_ref, H_got=None, H_ref=None):
     """Largest entry error in correlation scaling: |dS_xy| / sqrt(S_xx S_yy) and
     |dH_xy| / (sqrt(S_xx S_yy) (1 + |H_00|)) (row/column 0 has S_00 = 1)."""
@@ -36,6 +53,39 @@ def self_variation(oracle, O, G, E, w, offsets, n_keep, ref, **kw):
     Returns (|dE|, rel |d dmu|, max eigenvalue error, max subspace error)."""
     wr = None if w is None else w[::-1]
     r2 = oracle.blm_step(O[::-1], G[::-1], E[::-1], wr, offsets, n_keep, **kw)
+    de = abs(r2["e_pred"] - ref["e_pred"])
+    dd = rel_err(r2["dmu"], ref["dmu"])
+    dl = max(eig_err(a, b) for a, b in zip(r2["lam_b"], ref["lam_b"]))
+    ds = max(subspace_err(a, b) for a, b in zip(r2["B"], ref["B"]))
+    return de, dd, dl, ds
+
+
+def _eig_standard_route(H, S, *args, **kw):
+    """The generalized eigenproblem H v = lambda S v (S symmetric positive definite) through a
+    second backward-stable route: Cholesky S = L L^T, the standard eigenproblem of
+    L^-1 H L^-T (numpy's LAPACK geev), eigenvectors mapped back by L^-T."""
+    import scipy.linalg
+    L = np.linalg.cholesky(S)
+    A = scipy.linalg.solve_triangular(L, H, lower=True)
+    A = scipy.linalg.solve_triangular(L, A.T, lower=True).T
+    lam, V = np.linalg.eig(A)
+    V = scipy.linalg.solve_triangular(L.T, V, lower=False)
+    return lam, V
+
+
+def solver_variation(oracle, O, G, E, w, offsets, n_keep, ref, **kw):
+    """Sensitivity of the oracle's result to the eigen-solver itself: the same step with every
+    generalized eigenproblem solved through the Cholesky / standard-form route instead of QZ.
+    Two backward-stable solvers differ by the eigenvalues' condition numbers times the rounding
+    unit, which for these overlaps (condition 10^6 - 10^8) exceeds 1e-10.
+    Returns (|dE|, rel |d dmu|, max eigenvalue error, max subspace error)."""
+    import scipy.linalg
+    saved = scipy.linalg.eig
+    scipy.linalg.eig = _eig_standard_route
+    try:
+        r2 = oracle.blm_step(O, G, E, w, offsets, n_keep, **kw)
+    finally:
+        scipy.linalg.eig = saved
     de = abs(r2["e_pred"] - ref["e_pred"])
     dd = rel_err(r2["dmu"], ref["dmu"])
     dl = max(eig_err(a, b) for a, b in zip(r2["lam_b"], ref["lam_b"]))
@@ -109,9 +159,12 @@ def check_step_stagewise(oracle, got, ref, O, G, E, w, offsets, n_keep, tol_mat,
     oracle's against three times the first-order change the measured matrix differences predict;
     the combined matrices against the oracle's second sweep run with the GPU's B; E_pred and
     Delta mu against the oracle's combined solve and update on the GPU's combined matrices and B
-    (tol_own); and E_pred end to end against the independent oracle (tol_e).  Delta mu and the
-    retained subspaces end to end are reported, not asserted: they move with the block problems'
-    eigenvalue gaps, which the matrix tolerance already bounds."""
+    (tol_own); and E_pred end to end against the independent oracle (tol_e).
+    Delta mu and the retained subspaces end to end move with the block problems' eigenvalue
+    gaps and the overlap's conditioning (10^4 - 10^6 here), which amplify the matrix errors; at
+    the full step Delta mu differs from the FP64 path's by 2e-4 relative.  They are held to
+    bounds that catch a wrong selection or a wrong update, not to the matrix tolerance: Delta mu
+    1e-2 relative, retained subspaces 1e-4 (1 - cos of the largest principal angle)."""
     out = {}
     nb = len(offsets) - 1
     Bs = []
@@ -147,4 +200,6 @@ def check_step_stagewise(oracle, got, ref, O, G, E, w, offsets, n_keep, tol_mat,
     assert out["e_pred_own"] < tol_own * max(1.0, abs(e_own)), out
     assert out["dmu_own"] < 10 * tol_own, out
     assert out["e_pred"] < tol_e, out
+    assert out["dmu_end_to_end"] < 1e-2, out
+    assert out["block_subspace_end_to_end"] < 1e-4, out
     return out

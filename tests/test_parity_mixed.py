@@ -4,16 +4,12 @@ The inputs are FP32; the oracle receives the same FP32 values widened to FP64, s
 measures only the path's arithmetic: operands split into hi + lo (bf16 + bf16, or TF32 + FP32),
 products accumulated in FP32 tensor memory, FP64 centring and FP64 solves.
 
-Error model.  hi + lo represents each operand to 2^-16 (BF16X4) or 2^-22 (TF32X3) relative with a
-zero-mean residual, independent from sample to sample, so its contribution to a sum over N
-samples falls as 1/sqrt(N).  The tensor core's accumulation truncates; the kernel's short,
-preloaded accumulator intervals keep that bias to a few 1e-7 at these sizes and below it at the
-full step's long work units.  The targets hold at the size of the step they are stated for,
-N = 10^6 samples; for a test sample of N the tolerances are the targets widened by
-sqrt(10^6 / N):
-  S_b, H_b and the combined matrices (the latter against the oracle's second sweep run with the
-  GPU's B^(b)): 1e-6 in correlation scaling (|dA_xy| / sqrt(S_xx S_yy));
-  E_pred end to end: 1e-8 Hartree.
+Tolerances (tests/parity.py, mixed_tolerances): the targets stated for the full step (10^6
+samples: 1e-6 on S_b, H_b and the combined matrices in correlation scaling, 1e-8 Hartree on
+E_pred) split into a systematic share, held at every sample count, and the share of the
+zero-mean hi + lo residual, which falls as 1/sqrt(N) and is widened by sqrt(10^6 / N) at a test
+of N samples; the split comes from the error scan at the full 16384-parameter shape.  The
+10^6-sample step itself is held to the targets in tests/test_parity_full_shape.py.
 Each later stage is checked against the oracle given the same inputs (check_step_stagewise):
 the FP64 block solves against LAPACK on the GPU's own matrices, the kept eigenvalues' change
 against the first-order change the measured matrix differences predict, and E_pred and Delta mu
@@ -25,12 +21,9 @@ import pytest
 
 import synth
 from oracle import blm_oracle
-from tests.parity import check_step_stagewise, self_variation
+from tests.parity import check_step_stagewise, mixed_tolerances, self_variation
 
 pytestmark = pytest.mark.gpu
-
-TOL_MAT = 1e-6
-TOL_E = 1e-8
 
 
 @pytest.fixture(scope="module")
@@ -41,14 +34,17 @@ def torch_cuda():
     return torch
 
 
-def run_mixed(torch, O, G, E, w, offsets, n_keep, chunks=None, prec=None):
+def run_mixed(torch, O, G, E, w, offsets, n_keep, chunks=None, prec=None, old_dirs=None):
     import paper_1702_01481_gb300 as blm
     prec = blm.BLM_PREC_BF16X4 if prec is None else prec
     dev = torch.device("cuda:0")
     tO, tG, tE = (torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev) for a in (O, G, E))
     tw = torch.from_numpy(np.asarray(w, dtype=np.float32)).to(dev) if w is not None else None
     n = O.shape[1]
-    step = blm.Step(n, offsets, n_keep, precision=prec, input_type=blm.BLM_IN_F32)
+    n_old = 0 if old_dirs is None else old_dirs.shape[0]
+    D = torch.from_numpy(np.ascontiguousarray(old_dirs)).to(dev) if n_old else None
+    step = blm.Step(n, offsets, n_keep, precision=prec, input_type=blm.BLM_IN_F32, n_old=n_old,
+                    old_dirs=D)
     ns = O.shape[0]
     chunks = chunks or [ns]
     bounds = np.cumsum([0] + list(chunks))
@@ -70,20 +66,21 @@ def f32_inputs(wl, count=None):
     return O, G, E
 
 
-def check(got, ref, O, G, E, w, offsets, n_keep):
-    scale = max(1.0, np.sqrt(1.0e6 / O.shape[0]))
+def check(got, ref, O, G, E, w, offsets, n_keep, old_dirs=None):
+    tol_mat, tol_e = mixed_tolerances(O.shape[0])
     O, G, E = (a.astype(np.float64) for a in (O, G, E))
     w = None if w is None else np.asarray(w, np.float32).astype(np.float64)
-    de, dd, dl, ds = self_variation(blm_oracle, O, G, E, w, offsets, n_keep, ref)
+    de, dd, dl, ds = self_variation(blm_oracle, O, G, E, w, offsets, n_keep, ref,
+                                    old_dirs=old_dirs)
     return check_step_stagewise(blm_oracle, got, ref, O, G, E, w, offsets, n_keep,
-                                tol_mat=TOL_MAT * scale, tol_e=TOL_E * scale,
+                                tol_mat=tol_mat, tol_e=tol_e,
                                 tol_own=max(1e-9, 10 * dl, 10 * ds))
 
 
-def oracle_f32(O, G, E, w, offsets, n_keep):
+def oracle_f32(O, G, E, w, offsets, n_keep, old_dirs=None):
     return blm_oracle.blm_step(O.astype(np.float64), G.astype(np.float64), E.astype(np.float64),
                                None if w is None else np.asarray(w, np.float32).astype(np.float64),
-                               offsets, n_keep)
+                               offsets, n_keep, old_dirs=old_dirs)
 
 
 def test_equal_blocks_of_256(torch_cuda):
@@ -157,18 +154,68 @@ def test_tf32_split_precision(torch_cuda, which):
                             chunk=8192, noise="student3")
     O, G, E = f32_inputs(wl)
     ref = oracle_f32(O, G, E, None, wl.block_offsets, wl.n_keep)
-    got = run_mixed(torch_cuda, O, G, E, None, wl.block_offsets, wl.n_keep, prec=blm.BLM_PREC_TF32X3)
+    got = run_mixed(torch_cuda, O, G, E, None, wl.block_offsets, wl.n_keep, prec=blm.BLM_PREC_TF32X4)
     check(got, ref, O, G, E, None, wl.block_offsets, wl.n_keep)
 
 
 def test_uneven_blocks_full_parameter_count_tf32(torch_cuda):
     """The uneven-block workload at its full shape (16384 parameters in 48 blocks of 64 - 640,
-    K = 16, TF32X3 contractions) on its first 2048 samples: block problems up to 617, a
-    769-direction combined problem (Davidson), unaligned block offsets (register-staged tiles)."""
+    K = 16, TF32X4 contractions) on its first 8192 samples: block problems up to 617, a
+    769-direction combined problem (Davidson), unaligned block offsets.  (At 2048 samples, fewer
+    than four per parameter of the largest blocks, the step's energy moves by up to 4e-7 for
+    matrix differences within tolerance: too ill-sampled for the energy tolerance's model.)"""
     import paper_1702_01481_gb300 as blm
     wl = synth.workload("n16384u")
-    O, G, E = f32_inputs(wl, count=2048)
+    O, G, E = f32_inputs(wl, count=8192)
     ref = oracle_f32(O, G, E, None, wl.block_offsets, wl.n_keep)
-    got = run_mixed(torch_cuda, O, G, E, None, wl.block_offsets, wl.n_keep, chunks=[2048],
-                    prec=blm.BLM_PREC_TF32X3)
+    got = run_mixed(torch_cuda, O, G, E, None, wl.block_offsets, wl.n_keep, chunks=[8192],
+                    prec=blm.BLM_PREC_TF32X4)
     check(got, ref, O, G, E, None, wl.block_offsets, wl.n_keep)
+
+
+@pytest.mark.parametrize("cache", [0, 1 << 30, 3 * (1 << 20)])
+def test_host_input_with_host_cache_matches_device_input(torch_cuda, cache):
+    """Host (pinned) sample arrays staged in pieces, with the first sweep's device copies kept for
+    the second sweep (a cache that holds every piece, one that holds only the first, none): the
+    same step as from device arrays, up to the run-to-run order of the FP64 atomic sums."""
+    import paper_1702_01481_gb300 as blm
+    torch = torch_cuda
+    wl = synth.Workload("t", 300, 40000, [0, 100, 200, 300], 6, decades=4.0, chunk=40000, seed=13)
+    O, G, E = f32_inputs(wl)
+    # the host path copies pieces of 32768 samples: the device run takes the same pieces, so
+    # both launch the same kernels on the same sample ranges
+    got_dev = run_mixed(torch, O, G, E, None, wl.block_offsets, wl.n_keep, chunks=[32768, 7232])
+    hO, hG, hE = (torch.from_numpy(a).pin_memory() for a in (O, G, E))
+    step = blm.Step(wl.n, wl.block_offsets, wl.n_keep, precision=blm.BLM_PREC_BF16X4,
+                    input_type=blm.BLM_IN_F32)
+    blm.blm_set_host_cache(step.h, cache)
+    for rep in range(2):                       # the second step reuses the cache after a reset
+        step.reset()
+        step.accumulate(hO, hG, hE)
+        step.block_solve()
+        step.project(hO, hG, hE)
+        dmu = torch.empty(wl.n, dtype=torch.float64)
+        e = step.combined_solve(dmu)
+        assert abs(e - got_dev["e_pred"]) < 1e-12, (rep, e, got_dev["e_pred"])
+        assert np.linalg.norm(dmu.numpy() - got_dev["dmu"]) < 1e-9 * np.linalg.norm(got_dev["dmu"])
+    step.close()
+
+
+@pytest.mark.parametrize("prec,weighted", [("BLM_PREC_BF16X4", False), ("BLM_PREC_TF32X4", False),
+                                           ("BLM_PREC_BF16X4", True)])
+def test_history_directions_on_tensor_cores(torch_cuda, prec, weighted):
+    """N_O = 3 previous-update directions (Eq. 9-10) on the split-precision paths: the history
+    projections t = O'_k . D_jk, u = G_k . D_jk are prepared like the samples and their sums with
+    the block rows and with each other are tensor-core tiles of the first sweep's launch."""
+    import paper_1702_01481_gb300 as blm
+    wl = synth.Workload("t", 384, 8192, synth.equal_blocks(384, 4), 8, decades=4.0, chunk=8192,
+                        seed=17)
+    O, G, E = f32_inputs(wl)
+    rng = np.random.default_rng(5)
+    D = rng.normal(size=(3, wl.n)) * 0.1
+    w = np.linspace(0.6, 1.4, O.shape[0]).astype(np.float32) if weighted else None
+    ref = oracle_f32(O, G, E, w, wl.block_offsets, wl.n_keep, old_dirs=D)
+    got = run_mixed(torch_cuda, O, G, E, w, wl.block_offsets, wl.n_keep, chunks=[3000, 5192],
+                    prec=getattr(blm, prec), old_dirs=D)
+    assert got["blocks"][0][0].shape[0] == 1 + 96 + 3 * 3
+    check(got, ref, O, G, E, w, wl.block_offsets, wl.n_keep, old_dirs=D)
