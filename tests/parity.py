@@ -159,7 +159,13 @@ def check_step_stagewise(oracle, got, ref, O, G, E, w, offsets, n_keep, tol_mat,
     oracle's against three times the first-order change the measured matrix differences predict;
     the combined matrices against the oracle's second sweep run with the GPU's B; E_pred and
     Delta mu against the oracle's combined solve and update on the GPU's combined matrices and B
-    (tol_own); and E_pred end to end against the independent oracle (tol_e).
+    (tol_own); E_pred against the oracle's whole second half (block solves, second sweep over
+    the samples, combined solve) started from the GPU's block matrices (tol_e); and E_pred end to
+    end against the independent oracle, within tol_e or twice the oracle's own response to the
+    GPU's block matrices, whichever is larger.  That response is a property of the problem, not
+    of the GPU: where a block problem is sampled by fewer samples than it has parameters (the
+    16384-parameter uneven workload at 8192 samples) E_pred moves 40x more per unit of matrix
+    error than at the full step, while the block matrices themselves are held to tol_mat.
     Delta mu and the retained subspaces end to end move with the block problems' eigenvalue
     gaps and the overlap's conditioning (10^4 - 10^6 here), which amplify the matrix errors; at
     the full step Delta mu differs from the FP64 path's by 2e-4 relative.  They are held to
@@ -169,12 +175,14 @@ def check_step_stagewise(oracle, got, ref, O, G, E, w, offsets, n_keep, tol_mat,
     nb = len(offsets) - 1
     Bs = []
     em = esv = lam_ratio = es = 0.0
+    B_chain = []
     for b in range(nb):
         S, H, lam, B = got["blocks"][b]
         Bs.append(B)
         em = max(em, matrix_err(S, ref["S_b"][b], H, ref["H_b"][b]))
         m_b = offsets[b + 1] - offsets[b]
         lam_own, B_own, _ = oracle.block_solve(S, H, len(lam), m_b)
+        B_chain.append(B_own)
         esv = max(esv, eig_err(lam, lam_own), subspace_err(B, B_own))
         pred = eig_first_order(ref["S_b"][b], ref["H_b"][b], S, H, ref["lam_b"][b])
         dl = np.abs(np.asarray(lam) - np.asarray(ref["lam_b"][b]))
@@ -186,9 +194,13 @@ def check_step_stagewise(oracle, got, ref, O, G, E, w, offsets, n_keep, tol_mat,
     Sc_ref, Hc_ref = oracle.combined_matrices(O, G, E, w, offsets, Bs)
     ec = matrix_err(got["S_c"], Sc_ref, got["H_c"], Hc_ref)
     e_own, dmu_own = oracle.combined_update(got["S_c"], got["H_c"], offsets, Bs, m)
+    Sc_ch, Hc_ch = oracle.combined_matrices(O, G, E, w, offsets, B_chain)
+    e_chain, _ = oracle.combined_update(Sc_ch, Hc_ch, offsets, B_chain, m)
     out.update(block_matrix=em, own_solver=esv, block_eig_vs_first_order=lam_ratio,
                combined_matrix=ec, e_pred_own=abs(got["e_pred"] - e_own),
-               dmu_own=rel_err(got["dmu"], dmu_own), e_pred=abs(got["e_pred"] - ref["e_pred"]),
+               dmu_own=rel_err(got["dmu"], dmu_own), e_pred_vs_chain=abs(got["e_pred"] - e_chain),
+               oracle_response=abs(e_chain - ref["e_pred"]),
+               e_pred=abs(got["e_pred"] - ref["e_pred"]),
                block_subspace_end_to_end=es, dmu_end_to_end=rel_err(got["dmu"], ref["dmu"]))
     if report is not None:
         report.update(out)
@@ -199,7 +211,8 @@ def check_step_stagewise(oracle, got, ref, O, G, E, w, offsets, n_keep, tol_mat,
     assert lam_ratio <= 1.0, out
     assert out["e_pred_own"] < tol_own * max(1.0, abs(e_own)), out
     assert out["dmu_own"] < 10 * tol_own, out
-    assert out["e_pred"] < tol_e, out
+    assert out["e_pred_vs_chain"] < tol_e, out
+    assert out["e_pred"] < max(tol_e, 2.0 * out["oracle_response"]), out
     assert out["dmu_end_to_end"] < 1e-2, out
     assert out["block_subspace_end_to_end"] < 1e-4, out
     return out
