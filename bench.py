@@ -162,7 +162,7 @@ def run_ours(args, rank, world):
     prec = getattr(blm, PRECISIONS[args.precision])
     inp = blm.BLM_IN_F32 if mixed else blm.BLM_IN_F64
     step = blm.Step(n, wl.block_offsets, wl.n_keep, precision=prec, input_type=inp,
-                    stream=stream.cuda_stream)
+                    stream=stream.cuda_stream, pass_samples=args.pass_samples)
     dmu = torch.empty(n, dtype=torch.float64, device=dev)
 
     def one_step():
@@ -245,9 +245,7 @@ def run_ours(args, rank, world):
         ach = res["tc_pass1"]["tensor_tflops_executed"]
         roof = {"bound": "tensor", "achieved": ach, "peak": p, "unit": "TFLOP/s",
                 "frac": round(ach / p, 4), "traffic": profiled_traffic("tc_op_kernel_n16384.md"),
-                "kernel": ("tc_accumulate_kernel (first sweep, TF32 split converted in the kernel)"
-                           if args.precision == "tf32x4" else
-                           "tc_op_kernel (first sweep, prepared operands)"),
+                "kernel": "tc_op_kernel (first sweep, prepared %s operands)" % args.precision,
                 "per_launch_algorithmic_flop": exec_flop,
                 "peak_source": "measured bf16 sustained" if "bf16_tflops_sustained" in pk else "fallback"}
     elif kname == "contract_f64" and klaunch:
@@ -627,6 +625,8 @@ def main():
     ap.add_argument("--graph", action="store_true",
                     help="time the step as one captured CUDA graph (default for n16384u)")
     ap.add_argument("--samples", type=int, default=0)
+    ap.add_argument("--pass-samples", type=int, default=0,
+                    help="samples per internal pass (operand scratch size; 0: the library's 65536)")
     ap.add_argument("--cpu-samples", type=int, default=2048)
     ap.add_argument("--e2e-samples", type=int, default=524288,
                     help="samples of the end-to-end step (pinned host memory: 4 (2n + 1) bytes "

@@ -95,6 +95,10 @@ struct blm_handle {
   double* d_S = nullptr;         // block S matrices
   double* d_H = nullptr;
   double* d_eigw = nullptr;
+  std::vector<int32_t> eig_dims;           // block problem dimensions (team sizes of the solver)
+  int32_t cdim = 0;                        // combined problem dimension
+  void* d_teamctl = nullptr;               // team control blocks: nb block problems
+  void* d_cteamctl = nullptr;              // and the combined problem
   double* d_lam = nullptr;
   double* d_evec = nullptr;
   double* d_B = nullptr;
@@ -173,6 +177,8 @@ struct blm_batch {
   int nblocks_all = 0;
   EigProblem* d_comb = nullptr;           // the dense combined problems, one launch
   int ncomb_dense = 0;
+  std::vector<int32_t> blk_dims, comb_dims;   // their dimensions (team sizes)
+  void* d_teamctl = nullptr;              // team control blocks of both launches
   cudaGraphExec_t exec = nullptr;
   std::string err;
 };
@@ -417,6 +423,8 @@ void plan(blm_handle* h, Alloc& a) {
   a.add((void**)&h->d_S, 8 * SHsz);
   a.add((void**)&h->d_H, 8 * SHsz);
   a.add((void**)&h->d_eigw, 8 * EWsz);
+  a.add((void**)&h->d_teamctl, eig_team_ctl_bytes(h->nb));
+  a.add((void**)&h->d_cteamctl, eig_team_ctl_bytes(1));
   a.add((void**)&h->d_lam, 8 * LOsz);
   a.add((void**)&h->d_evec, 8 * VOsz);
   a.add((void**)&h->d_B, 8 * BOsz);
@@ -804,7 +812,7 @@ blm_status enqueue_block_solve(blm_handle* h) {
   if (s != BLM_OK) return s;
   {
     Prof pr(h, PC_EIG_BLOCKS);
-    launch_eig(h->d_eigp, h->nb, 512, h->st);
+    launch_eig(h->d_eigp, h->nb, 512, h->st, h->eig_dims.data(), h->d_teamctl);
   }
   s = block_solve_post(h);
   if (s != BLM_OK) return s;
@@ -849,13 +857,13 @@ blm_status combined_eig(blm_handle* h) {
   cudaStream_t st = h->st;
   Prof pr(h, PC_EIG_COMBINED);
   if (combined_is_dense(h)) {
-    launch_eig(h->d_ceigp, 1, 512, st);
+    launch_eig(h->d_ceigp, 1, 512, st, &h->cdim, h->d_cteamctl);
   } else {
     BLM_CU(h, launch_davidson(h->d_ceigp, kDavidsonTol, kDavidsonIter, h->d_ceigw,
                               (int)(h->dc + 1), st));
     // a Davidson run that did not converge (clustered or ill-conditioned combined problems
     // from few samples) falls back to the dense solver on the same matrices
-    launch_eig(h->d_ceigp + 1, 1, 512, st);
+    launch_eig(h->d_ceigp + 1, 1, 512, st, &h->cdim, h->d_cteamctl);
   }
   return BLM_OK;
 }
@@ -989,8 +997,11 @@ blm_status blm_create(const blm_problem* p, void* stream, blm_handle** out) {
     std::vector<BlockAsm> ba(h->nb);
     std::vector<EigProblem> ep(h->nb);
     std::vector<DirBlock> dbk(h->nb);
+    h->eig_dims.assign(h->nb, 0);
+    h->cdim = (int32_t)(h->dc + 1);
     for (int b = 0; b < h->nb; ++b) {
       const int64_t D = h->db[b] + 1;
+      h->eig_dims[b] = (int32_t)D;
       pbB[b] = ProjBlock{h->off[b], h->Mb[b], h->Kb[b], h->oc[b], 0, h->d_B + h->B_off[b], h->Mb[b],
                          h->d_B32 + h->B_off[b]};
       pbD[b] = ProjBlock{h->off[b], h->Mb[b], h->n_old, b * h->n_old, 0,
@@ -998,14 +1009,14 @@ blm_status blm_create(const blm_problem* p, void* stream, blm_handle** out) {
                          h->d_D32 ? h->d_D32 + h->off[b] : nullptr};
       ba[b] = BlockAsm{h->off[b], h->Mb[b], h->db[b], b, 0, h->d_C + h->C_off[b],
                        h->d_S + h->SH_off[b], h->d_H + h->SH_off[b]};
-      ep[b] = EigProblem{(int)D, h->Kb[b], 0, 0, h->d_S + h->SH_off[b], h->d_H + h->SH_off[b],
+      ep[b] = EigProblem{(int)D, h->Kb[b], 0, kEigLocate32, h->d_S + h->SH_off[b], h->d_H + h->SH_off[b],
                          h->d_eigw + h->eigw_off[b], h->d_lam + h->lam_off[b],
                          h->d_evec + h->vec_off[b], h->d_status + b};
       dbk[b] = DirBlock{h->Mb[b], h->Kb[b], (int)D, 0, h->d_evec + h->vec_off[b],
                         h->d_B + h->B_off[b], h->d_status + b};
     }
     std::vector<EigProblem> cp(2);
-    cp[0] = EigProblem{(int)(h->dc + 1), 1, 1, 0, h->d_Sc, h->d_Hc, h->d_ceigw, h->d_clam,
+    cp[0] = EigProblem{(int)(h->dc + 1), 1, 1, kEigLocate32, h->d_Sc, h->d_Hc, h->d_ceigw, h->d_clam,
                        h->d_cev, h->d_status + h->nb, nullptr};
     cp[1] = cp[0];
     cp[1].run_if_noconv = h->d_status + h->nb;
@@ -1326,6 +1337,7 @@ blm_status blm_batch_destroy(blm_batch* b) {
   if (b->cap_st) cudaStreamDestroy(b->cap_st);
   if (b->d_blocks) cudaFree(b->d_blocks);
   if (b->d_comb) cudaFree(b->d_comb);
+  if (b->d_teamctl) cudaFree(b->d_teamctl);
   delete b;
   return BLM_OK;
 }
@@ -1356,7 +1368,11 @@ blm_status blm_batch_create(const blm_problem* problems, int32_t count, void* st
       break;
     }
     blocks.insert(blocks.end(), ep.begin(), ep.end());
-    if (combined_is_dense(h)) comb.push_back(cp[0]);
+    b->blk_dims.insert(b->blk_dims.end(), h->eig_dims.begin(), h->eig_dims.end());
+    if (combined_is_dense(h)) {
+      comb.push_back(cp[0]);
+      b->comb_dims.push_back(h->cdim);
+    }
   }
   if (s == BLM_OK) {
     b->nblocks_all = (int)blocks.size();
@@ -1365,6 +1381,9 @@ blm_status blm_batch_create(const blm_problem* problems, int32_t count, void* st
     bool ok = cudaMalloc((void**)&b->d_blocks, sizeof(EigProblem) * blocks.size()) == cudaSuccess &&
               cudaMemcpy(b->d_blocks, blocks.data(), sizeof(EigProblem) * blocks.size(),
                          cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok)
+      ok = cudaMalloc(&b->d_teamctl, eig_team_ctl_bytes((int)blocks.size() + (int)comb.size())) ==
+           cudaSuccess;
     if (ok && !comb.empty())
       ok = cudaMalloc((void**)&b->d_comb, sizeof(EigProblem) * comb.size()) == cudaSuccess &&
            cudaMemcpy(b->d_comb, comb.data(), sizeof(EigProblem) * comb.size(),
@@ -1478,7 +1497,8 @@ blm_status blm_batch_capture(blm_batch* b, const void* const* O, const void* con
       if (s == BLM_OK) s = block_solve_pre(b->hs[i]);
     }
     join();
-    if (s == BLM_OK) launch_eig(b->d_blocks, b->nblocks_all, 512, b->cap_st);
+    if (s == BLM_OK)
+      launch_eig(b->d_blocks, b->nblocks_all, 512, b->cap_st, b->blk_dims.data(), b->d_teamctl);
     fork();
     for (int i = 0; s == BLM_OK && i < count; ++i) {
       s = block_solve_post(b->hs[i]);
@@ -1486,7 +1506,9 @@ blm_status blm_batch_capture(blm_batch* b, const void* const* O, const void* con
       if (s == BLM_OK) s = combined_pre(b->hs[i]);
     }
     join();
-    if (s == BLM_OK && b->ncomb_dense > 0) launch_eig(b->d_comb, b->ncomb_dense, 512, b->cap_st);
+    if (s == BLM_OK && b->ncomb_dense > 0)
+      launch_eig(b->d_comb, b->ncomb_dense, 512, b->cap_st, b->comb_dims.data(),
+                 static_cast<char*>(b->d_teamctl) + eig_team_ctl_bytes(b->nblocks_all));
     // combined problems above the dense limit: Davidson (a cooperative grid over every SM),
     // one at a time on the origin stream while no branch runs
     for (int i = 0; s == BLM_OK && i < count; ++i)

@@ -234,6 +234,7 @@ struct Shared {
   int sel_part[kMaxKeep];   // 0 real, 1 real part of complex, 2 imaginary part of complex
   int job_q0[kMaxKeep];     // eigenvector jobs: selection entries [job_q0, job_q0 + job_len)
   int job_len[kMaxKeep];
+  int out_pos[kMaxKeep];    // output position of each selection entry (ascending eigenvalues)
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -414,6 +415,7 @@ __device__ __forceinline__ void chase_sync() {
 // shared memory the QR needs: the window and the reflectors of one window (all bulges)
 constexpr int kQrSmemDoubles = kWin * kWinLd + 4 * kWin * kNbMax;
 static_assert(kChase == 32 * kNbMax, "one chase warp per bulge slot");
+static_assert(kEigThreads == kNbMax * kWin, "one thread per (window row or column, bulge slot)");
 
 // Arithmetic of the QR sweep: FP64, or double words (default; FP64 when it fails).
 template <typename R>
@@ -438,14 +440,15 @@ struct QrArith<dw> {
 // shift pairs in sh.shf.  Bulge j starts three steps after bulge j - 1 and, at time step tau,
 // takes step k_j = l + tau - 3 j (active for l <= k_j <= hi - 1); bulges three rows apart touch
 // disjoint rows in their row operations and disjoint columns in their column operations, so one
-// time step applies all of them between two barriers:
-//   phase 1 (thread t owns column a + t): every thread forms every active bulge's reflector from
-//     its bulge column (or, at k_j = l, from the shift polynomial's first column) and applies
-//     the row operations to its column;
-//   phase 2 (thread t owns row a + t): leading bulge first, set the bulge column to (alpha, 0, 0)
-//     and apply the column operations -- a row where a trailing bulge's column operation meets
-//     the leading bulge's annihilated column receives the annihilation first, as in the
-//     unpipelined order.
+// time step applies all of them between barriers:
+//   phase 0: warp j forms bulge j's reflector from its bulge column (or, at k_j = l, from the
+//     shift polynomial's first column);
+//   phase 1 (one thread per window column and bulge): the row operations;
+//   phase 2 (one thread per window row and bulge): set the bulge column to (alpha, 0, 0) and
+//     apply the column operations.  The one entry two bulges share -- row k_j + 3 of the
+//     leading bulge's annihilated column, which the trailing bulge's column operation covers --
+//     takes the leading bulge's alpha as the trailing operation's input and keeps the trailing
+//     operation's result, as in the unpipelined order.
 // Rows above and columns right of the window receive the same operations afterwards from the
 // stored reflectors, all bulges of one time step on a sliding run of 3 kNbMax entries (their
 // ranges are disjoint and adjacent), time steps in order.
@@ -467,12 +470,15 @@ __device__ void multi_sweep(R* G, int m, int l, int hi, int nb, R* win, R* refl,
       win[r * kWinLd + c] = g(a + r, a + c);
     }
     __syncthreads();
-    if (t < kChase) {
+    {
       auto W = [&](int i, int j) -> R& { return win[(i - a) * kWinLd + (j - a)]; };
       auto clampw = [&](int i) { return min(max(i, a), b); };
+      // phases 1 and 2 run one thread per (column or row, slot): slot js = t / kWin of the
+      // window's column or row a + (t mod kWin) (blockDim = kNbMax * kWin)
+      const int js = t / kWin, tl = t - js * kWin;
       for (int tau = ts; tau <= te; ++tau) {
         R* rft = refl + (tau - ts) * kNbMax * 4;   // (beta, v1, v2, alpha) of each slot
-        {
+        if (t < kChase) {
           // phase 0: warp j forms slot j's reflector from its bulge column (or, at k = l, from
           // the shift polynomial's first column)
           const int j = t >> 5;
@@ -503,80 +509,56 @@ __device__ void multi_sweep(R* G, int m, int l, int hi, int nb, R* win, R* refl,
             rft[4 * j + 3] = al;
           }
         }
-        chase_sync();
-        // phases 1 and 2: every slot's work from clamped (valid) indices, kept or dropped by
-        // predicated stores, so that the slots' dependent chains overlap
-        R be[kNbMax], v1[kNbMax], v2[kNbMax], al[kNbMax], bv1[kNbMax], bv2[kNbMax];
-        bool act[kNbMax];
-#pragma unroll
-        for (int j = 0; j < kNbMax; ++j) {
-          const int k = l + tau - 3 * j;
-          be[j] = rft[4 * j];
-          v1[j] = rft[4 * j + 1];
-          v2[j] = rft[4 * j + 2];
-          al[j] = rft[4 * j + 3];
-          act[j] = j < nb && k >= l && k <= hi - 1;
-          bv1[j] = be[j] * v1[j];
-          bv2[j] = be[j] * v2[j];
-        }
-        const int c = a + t;   // phase 1: row operations on column c (slots touch disjoint rows)
-        if (c <= b) {
-          R n[kNbMax][3];
-#pragma unroll
-          for (int j = 0; j < kNbMax; ++j) {
-            const int k = l + tau - 3 * j;
-            const R r0 = W(clampw(k), c), r1 = W(clampw(k + 1), c), r2 = W(clampw(k + 2), c);
-            const R p = r0 + (v1[j] * r1 + v2[j] * r2);
-            n[j][0] = r0 - be[j] * p;
-            n[j][1] = r1 - bv1[j] * p;
-            n[j][2] = r2 - bv2[j] * p;
-          }
-#pragma unroll
-          for (int j = 0; j < kNbMax; ++j) {
-            const int k = l + tau - 3 * j;
-            if (act[j] && mag(be[j]) != 0 && c >= k) {
-              W(k, c) = n[j][0];
-              W(k + 1, c) = n[j][1];
-              if (k <= hi - 2) W(k + 2, c) = n[j][2];
-            }
+        __syncthreads();
+        const int k = l + tau - 3 * js;
+        const R be = rft[4 * js], v1 = rft[4 * js + 1], v2 = rft[4 * js + 2], al = rft[4 * js + 3];
+        const bool act = js < nb && k >= l && k <= hi - 1 && mag(be) != 0;
+        const R bv1 = be * v1, bv2 = be * v2;
+        const bool three = k <= hi - 2;
+        // phase 1: row operations of slot js on column c (the slots' rows are disjoint)
+        {
+          const int c = a + tl;
+          if (act && c <= b && c >= k) {
+            const R r0 = W(k, c), r1 = W(k + 1, c), r2 = three ? W(k + 2, c) : zero;
+            const R p = r0 + (v1 * r1 + v2 * r2);
+            W(k, c) = r0 - be * p;
+            W(k + 1, c) = r1 - bv1 * p;
+            if (three) W(k + 2, c) = r2 - bv2 * p;
           }
         }
-        chase_sync();
-        const int r = a + t;   // phase 2: bulge columns and column operations on row r
-        if (r <= b) {
-          R n[kNbMax][3];
-#pragma unroll
-          for (int j = 0; j < kNbMax; ++j) {
-            const int k = l + tau - 3 * j;
-            const R c0 = W(r, clampw(k)), c1 = W(r, clampw(k + 1));
-            R c2 = W(r, clampw(k + 2));
-            if (j > 0) {
-              // column k + 2 is the leading slot's bulge column; on its row k + 3 that slot
-              // writes alpha first (below), which this slot's operation must see
-              const int kl = k + 3;
-              if (act[j - 1] && mag(be[j - 1]) != 0 && kl > l && r == kl) c2 = al[j - 1];
+        __syncthreads();
+        // phase 2: slot js's bulge column and column operations on row r.  Column k + 2 is the
+        // leading slot's (js - 1) annihilated bulge column: on its row k + 3 that slot's alpha
+        // enters this operation, and this slot's result is what the entry keeps (the leading
+        // slot leaves its alpha unwritten there).
+        {
+          const int r = a + tl;
+          if (act && r <= b) {
+            const int kt = k - 3;   // the trailing slot (js + 1)
+            bool trail = false;
+            if (js + 1 < nb && kt >= l) {
+              const R bt = rft[4 * (js + 1)];
+              trail = mag(bt) != 0 && kt <= hi - 2;
             }
-            const R p = c0 + (v1[j] * c1 + v2[j] * c2);
-            n[j][0] = c0 - be[j] * p;
-            n[j][1] = c1 - bv1[j] * p;
-            n[j][2] = c2 - bv2[j] * p;
-          }
-#pragma unroll
-          for (int j = 0; j < kNbMax; ++j) {
-            const int k = l + tau - 3 * j;
-            if (act[j] && mag(be[j]) != 0) {
-              const bool three = k <= hi - 2;
-              if (k > l && r >= k && r <= k + (three ? 2 : 1)) W(r, k - 1) = (r == k) ? al[j] : zero;
-              const int rmax = three ? min(k + 3, hi) : hi;
-              if (r <= rmax) {
-                W(r, k) = n[j][0];
-                W(r, k + 1) = n[j][1];
-                if (three) W(r, k + 2) = n[j][2];
+            if (k > l && r >= k && r <= k + (three ? 2 : 1) && !(r == k && trail))
+              W(r, k - 1) = (r == k) ? al : zero;
+            const int rmax = three ? min(k + 3, hi) : hi;
+            if (r <= rmax) {
+              const R c0 = W(r, k), c1 = W(r, k + 1);
+              R c2 = three ? W(r, k + 2) : zero;
+              if (js > 0 && three && r == k + 3) {
+                const int kl = k + 3;   // the leading slot's step
+                const R bl = rft[4 * (js - 1)];
+                if (kl <= hi - 1 && mag(bl) != 0) c2 = rft[4 * (js - 1) + 3];
               }
+              const R p = c0 + (v1 * c1 + v2 * c2);
+              W(r, k) = c0 - be * p;
+              W(r, k + 1) = c1 - bv1 * p;
+              if (three) W(r, k + 2) = c2 - bv2 * p;
             }
           }
         }
-        chase_sync();
+        __syncthreads();
       }
     }
     __syncthreads();
@@ -923,8 +905,13 @@ static_assert(kQrSmemDoubles <= kEigSmemDoubles, "QR window exceeds the solver's
 // Workspace of dense_geig for dimension m: L, A, Hh (m^2 each), W (2 m^2), 6 vectors of m;
 // then the per-warp factors and pivots and the kMaxKeep Hessenberg-basis eigenvectors.
 __host__ __device__ constexpr int64_t eig_base_doubles(int64_t m) { return 5 * m * m + 6 * m; }
+constexpr int kMaxTeam = 8;                             // CTAs per problem at most
+// ranks 1.. of a team keep their two scratch vectors after the eigenvector section
+__host__ __device__ constexpr int64_t eig_rank_offset(int64_t m) {
+  return eig_base_doubles(m) + kVecWarps * m * (m + 1) + kVecWarps * 3 * m + kMaxKeep * 2 * m;
+}
 __host__ __device__ constexpr int64_t eig_total_doubles(int64_t m) {
-  return eig_base_doubles(m) + kVecWarps * m * (m + 1) + kVecWarps * 3 * m + kMaxKeep * 2 * m + 64;
+  return eig_rank_offset(m) + (int64_t)(kMaxTeam - 1) * 2 * m + 64;
 }
 
 __device__ __forceinline__ int64_t urow(int k, int m) {
@@ -1183,10 +1170,121 @@ __device__ __forceinline__ void rows4_dot_axpy(double* a, int64_t ld, int i0, in
   rows4_axpy(a, ld, i0, stride, iend, sc, j1r, x, j0, lane);
 }
 
-// Dense solver for one problem, run by the whole CTA (dsm: up to 200 KB of shared memory).
-__device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
+
+// ---------------------------------------------------------------------------------------------
+// Teams: one problem solved by T CTAs of a cooperative launch (all resident), which meet at a
+// bounded barrier on a per-problem control block in global memory (zeroed before the launch).
+// A wait that runs out marks the block, and every rank then gives up at its next barrier.
+// ---------------------------------------------------------------------------------------------
+constexpr uint32_t kTeamSpinLimit = 1u << 26;
+struct TeamCtl {
+  unsigned int count, gen;  // barrier arrivals, generation
+  int err;                  // a barrier gave up
+  int flag;                 // a rank's early status (ST_*), read after a barrier
+  int qr_ok;                // rank 0's QR: 1 located in FP32, 2 in double words or FP64, 0 failed
+  int vec_fail;             // an eigenvector that is no eigenvector (double-word location)
+  unsigned long long anorm_bits;   // max |Hessenberg entry| as the bits of a non-negative double
+  double sel_err[kMaxKeep]; // FP32 location: |FP64 quotient - FP32 value| per kept entry
+  double sel_qim[kMaxKeep]; // and the FP64 quotient's imaginary part (complex entries)
+};
+struct Team {
+  int r, T;
+  TeamCtl* ctl;
+};
+
+__device__ bool team_sync(const Team& tm, TeamCtl* c, int* ok_smem) {
+  __syncthreads();
+  if (tm.T == 1) return true;
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = &c->gen;
+    const unsigned int g = *vgen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&c->count, 1u) == (unsigned int)tm.T - 1) {
+      atomicExch(&c->count, 0u);
+      __threadfence();
+      atomicAdd(&c->gen, 1u);
+    } else {
+      uint32_t i = 0;
+      while (*vgen == g) {
+        if (++i > kTeamSpinLimit || *(volatile int*)&c->err) {
+          ok = 0;
+          atomicExch(&c->err, 1);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    if (*(volatile int*)&c->err) ok = 0;
+    __threadfence();
+    *ok_smem = ok;
+  }
+  __syncthreads();
+  return *ok_smem != 0;
+}
+
+// Column pieces of 32: piece p belongs to rank p mod T.  The first piece of rank R that holds a
+// column >= j0.
+__device__ __forceinline__ int first_piece(int j0, int R, int T) {
+  const int p = j0 >> 5;
+  return p + ((R - p) % T + T) % T;
+}
+// a[j] -= s * x[j] for this rank's columns j in [j0, j1)
+__device__ __forceinline__ void row_axpy_own(double* __restrict__ a, const double* __restrict__ x,
+                                             double s, int j0, int j1, int lane, int R, int T) {
+  for (int p = first_piece(j0, R, T); 32 * p < j1; p += T) {
+    const int j = 32 * p + lane;
+    if (j >= j0 && j < j1) a[j] -= s * x[j];
+  }
+}
+// rows4_axpy over this rank's column pieces (four pieces per pass; T = 1: 128 contiguous columns)
+__device__ __forceinline__ void rows4_axpy_own(double* a, int64_t ld, int i0, int stride, int iend,
+                                               const double* s, const int* j1, const double* x,
+                                               int j0, int lane, int R, int T) {
+  int jmax = j0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+    if (i0 + r * stride < iend) jmax = max(jmax, j1[r]);
+  for (int p = first_piece(j0, R, T); 32 * p < jmax; p += 4 * T) {
+    double v[4][4], xv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = 32 * (p + q * T) + lane;
+      xv[q] = (j >= j0 && j < jmax) ? x[j] : 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = i0 + r * stride, j = 32 * (p + q * T) + lane;
+        v[r][q] = (i < iend && j >= j0 && j < j1[r]) ? a[(int64_t)i * ld + j] : 0.0;
+      }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = i0 + r * stride, j = 32 * (p + q * T) + lane;
+        if (i < iend && j >= j0 && j < j1[r]) a[(int64_t)i * ld + j] = v[r][q] - s[r] * xv[q];
+      }
+  }
+}
+
+// Dense solver for one problem, run by a team of T CTAs (T = 1: one CTA; dsm: up to 200 KB of
+// shared memory per CTA).  The FP64 reductions are shared out: the scaling, the two triangular
+// solves, the Hessenberg reduction (columns for its left, rows for its right updates), the
+// inverse iterations and the back-transformations; the Cholesky factorisation and the QR run
+// on rank 0 while the others wait at the team barrier.  Every rank takes the same decisions
+// from the same data (values read after a barrier), so the ranks leave together.
+__device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh, Team tm = Team{0, 1, nullptr}) {
   const int m = pb.m;
   const int t = threadIdx.x, nt = blockDim.x;
+  __shared__ TeamCtl local_ctl;
+  __shared__ int bar_ok;
+  const int R = tm.r, T = tm.T;
+  TeamCtl* ctl = T > 1 ? tm.ctl : &local_ctl;
+  auto sync = [&]() -> bool { return team_sync(tm, ctl, &bar_ok); };
+  // column pieces of 32 belong to rank (piece mod T); rows to the team's warps in turn
+  auto own_col = [&](int j) { return ((j >> 5) % T) == R; };
   const int64_t mm = (int64_t)m * m;
   double* L = pb.work;
   double* A = L + mm;
@@ -1196,8 +1294,9 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
   double* hbeta = dsc + m;
   double* wr = hbeta + m;
   double* wi = wr + m;
-  double* col = wi + m;           // m
-  double* vtmp = col + m;         // m
+  // per-rank vectors (m each): rank 0 in the base area, the others after the last section
+  double* col = tm.r == 0 ? wi + m : pb.work + eig_rank_offset(m) + (int64_t)(tm.r - 1) * 2 * m;
+  double* vtmp = col + m;
   // per-warp inverse iteration: packed U, pivots; then the Hessenberg-basis eigenvectors
   double* Uw = pb.work + eig_base_doubles(m);                 // kVecWarps x m (m + 1)
   double* plw = Uw + (int64_t)kVecWarps * m * (m + 1);        // kVecWarps x 2m
@@ -1211,43 +1310,54 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
   if (t == 0) {
     sh.iscal[1] = ST_OK;
     sh.iscal[4] = 0;
+    if (T == 1) {
+      local_ctl.flag = ST_OK;
+      local_ctl.qr_ok = 0;
+      local_ctl.vec_fail = 0;
+      local_ctl.anorm_bits = 0ull;
+    }
   }
   __syncthreads();
+  const int rw = t >> 5, rl = t & 31, rnw = nt >> 5;
+  const int gw = R * rnw + rw, gnw = T * rnw;   // this warp among the team's warps
+  auto own_row = [&](int i) { return (i % gnw) / rnw == R; };
+  // the team's status word: any rank may set it; read after a barrier
+  auto flag = [&]() { return *(volatile int*)&ctl->flag; };
+  auto fail = [&](int code) {
+    if (t == 0) *pb.status = code;
+  };
   // ---- 1. scaling ----
+  // (every rank needs all of dsc: each computes it into shared memory, rank 0 keeps the copy
+  // the back-transformation reads)
+  double* dscs = dsm;
   for (int i = t; i < m; i += nt) {
     const double s = pb.S[(int64_t)i * m + i];
-    if (!(s > 0.0) || !isfinite(s)) sh.iscal[1] = ST_NOT_PD;
-    dsc[i] = (s > 0.0) ? 1.0 / sqrt(s) : 0.0;
+    if (!(s > 0.0) || !isfinite(s)) ctl->flag = ST_NOT_PD;
+    const double d = (s > 0.0) ? 1.0 / sqrt(s) : 0.0;
+    dscs[i] = d;
+    if (R == 0) dsc[i] = d;
   }
   __syncthreads();
-  if (sh.iscal[1] != ST_OK) {
-    if (t == 0) *pb.status = sh.iscal[1];
-    return;
-  }
-  // (rows over warps, columns over lanes: coalesced, no index division)
-  const int rw = t >> 5, rl = t & 31, rnw = nt >> 5;
-  for (int i = rw; i < m; i += rnw) {
-    const double di = dsc[i];
+  // (rows over the team's warps, columns over lanes: coalesced, no index division)
+  for (int i = gw; i < m; i += gnw) {
+    const double di = dscs[i];
     for (int j = rl; j < m; j += 32) {
       const int64_t idx = (int64_t)i * m + j;
-      const double sv = pb.S[idx] * di * dsc[j];
-      const double hv = pb.H[idx] * di * dsc[j];
-      if (!isfinite(sv) || !isfinite(hv)) sh.iscal[1] = ST_NONFINITE;
+      const double sv = pb.S[idx] * di * dscs[j];
+      const double hv = pb.H[idx] * di * dscs[j];
+      if (!isfinite(sv) || !isfinite(hv)) ctl->flag = ST_NONFINITE;
       L[idx] = sv;
       A[idx] = hv;
     }
   }
-  __syncthreads();
-  if (sh.iscal[1] != ST_OK) {
-    if (t == 0) *pb.status = sh.iscal[1];
-    return;
-  }
+  if (!sync()) return fail(ST_NOCONV);
+  if (flag() != ST_OK) return fail(flag());
   EIG_MARK(1);
   // The Davidson projection's overlap is the identity (S-orthonormal basis): L = I and A = H
   // as assembled above, so the Cholesky factorisation and the reduction are skipped.
-  if (!pb.fp32_locate) {
-    // ---- 2a. Cholesky (right-looking, lower) ----
-    for (int k = 0; k < m; ++k) {
+  if (!(pb.flags & kEigUnitS)) {
+    // ---- 2a. Cholesky (right-looking, lower), rank 0 ----
+    for (int k = 0; k < m && R == 0; ++k) {
       if (t == 0) {
         const double p = L[(int64_t)k * m + k];
         if (!(p > 1e-15)) {
@@ -1284,14 +1394,15 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
       }
       __syncthreads();
     }
-    if (sh.iscal[1] != ST_OK) {
-      if (t == 0) *pb.status = sh.iscal[1];
-      return;
-    }
-    // ---- 2b. A <- L^-1 A (row forward substitution) ----
+    if (R == 0 && t == 0 && sh.iscal[1] != ST_OK) ctl->flag = sh.iscal[1];
+    if (!sync()) return fail(ST_NOCONV);
+    if (flag() != ST_OK) return fail(flag());
+    // ---- 2b. A <- L^-1 A (row forward substitution; columns are independent: each rank
+    // takes its column pieces) ----
     for (int k = 0; k < m; ++k) {
       const double inv = 1.0 / L[(int64_t)k * m + k];
       for (int j = t; j < m; j += nt) {
+        if (!own_col(j)) continue;
         const double v = A[(int64_t)k * m + j] * inv;
         A[(int64_t)k * m + j] = v;
         col[j] = v;
@@ -1299,7 +1410,7 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
       __syncthreads();
       if (m <= kRows4Min) {
         for (int i = k + 1 + rw; i < m; i += rnw)
-          row_axpy(A + (int64_t)i * m, col, L[(int64_t)i * m + k], 0, m, rl);
+          row_axpy_own(A + (int64_t)i * m, col, L[(int64_t)i * m + k], 0, m, rl, R, T);
       } else {
         for (int i = k + 1 + rw; i < m; i += 4 * rnw) {
           double sv[4];
@@ -1310,41 +1421,48 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
             sv[r] = ir < m ? L[(int64_t)ir * m + k] : 0.0;
             j1[r] = m;
           }
-          rows4_axpy(A, m, i, rnw, m, sv, j1, col, 0, rl);
+          rows4_axpy_own(A, m, i, rnw, m, sv, j1, col, 0, rl, R, T);
         }
       }
       __syncthreads();
     }
-    // ---- 2c. A <- A L^-T (column forward substitution) ----
+    if (!sync()) return fail(ST_NOCONV);
+    // ---- 2c. A <- A L^-T (column forward substitution; rows are independent: each rank
+    // takes its rows) ----
     for (int k = 0; k < m; ++k) {
       const double inv = 1.0 / L[(int64_t)k * m + k];
       for (int i = t; i < m; i += nt) {
+        vtmp[i] = L[(int64_t)i * m + k];            // column k of L, read once
+        if (!own_row(i)) continue;
         const double v = A[(int64_t)i * m + k] * inv;
         A[(int64_t)i * m + k] = v;
         col[i] = v;
-        vtmp[i] = L[(int64_t)i * m + k];            // column k of L, read once
       }
       __syncthreads();
       if (m <= kRows4Min) {
-        for (int i = rw; i < m; i += rnw) row_axpy(A + (int64_t)i * m, vtmp, col[i], k + 1, m, rl);
+        for (int i = gw; i < m; i += gnw) row_axpy(A + (int64_t)i * m, vtmp, col[i], k + 1, m, rl);
       } else {
-        for (int i = rw; i < m; i += 4 * rnw) {
+        for (int i = gw; i < m; i += 4 * gnw) {
           double sv[4];
           int j1[4];
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
-            const int ir = i + r * rnw;
+            const int ir = i + r * gnw;
             sv[r] = ir < m ? col[ir] : 0.0;
             j1[r] = m;
           }
-          rows4_axpy(A, m, i, rnw, m, sv, j1, vtmp, k + 1, rl);
+          rows4_axpy(A, m, i, gnw, m, sv, j1, vtmp, k + 1, rl);
         }
       }
       __syncthreads();
     }
+    if (!sync()) return fail(ST_NOCONV);
   }
   EIG_MARK(2);
   // ---- 3. Householder reduction to Hessenberg form ----
+  // Every rank forms column k's reflector from the same data; the left update (a reduction
+  // over rows) is shared out by column pieces, the right update (a reduction over columns) by
+  // rows, with a team barrier after each.
   for (int k = 0; k < m - 2; ++k) {
     double part = 0.0;
     for (int i = k + 2 + t; i < m; i += nt) {
@@ -1366,19 +1484,19 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
     }
     __syncthreads();
     const double beta = sh.scal[1], v0 = sh.scal[2];
-    if (t == 0) hbeta[k] = beta;
+    if (t == 0 && R == 0) hbeta[k] = beta;
     // u = (1, x[1:]/v0) into col[k+1..m-1]
     const double rv0 = rcp_nr(v0);
     for (int i = k + 1 + t; i < m; i += nt) col[i] = (i == k + 1) ? 1.0 : A[(int64_t)i * m + k] * rv0;
     __syncthreads();
     if (beta != 0.0) {
-      // left: rows k+1.., columns k..: w = beta u^T A from per-warp partial sums over rows
-      // (each warp a slice of the rows, lanes over columns: coalesced, loads independent),
-      // then A -= u w
+      // left: rows k+1.., this rank's columns k..: w = beta u^T A from per-warp partial sums
+      // over rows (each warp a slice of the rows, lanes over columns: coalesced, loads
+      // independent), then A -= u w
       double* wpart = dsm;                          // rnw x m (shared memory is free here)
-      for (int jc = k; jc < m; jc += 32) {
-        const int j = jc + rl;
-        if (j < m) {
+      for (int p = first_piece(k, R, T); 32 * p < m; p += T) {
+        const int j = 32 * p + rl;
+        if (j >= k && j < m) {
           const double* __restrict__ aj = A + j;
           const double* __restrict__ u = col;
           double acc0 = 0.0, acc1 = 0.0;
@@ -1393,13 +1511,15 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
       }
       __syncthreads();
       for (int j = k + t; j < m; j += nt) {
+        if (!own_col(j)) continue;
         double sum = 0.0;
         for (int w2 = 0; w2 < rnw; ++w2) sum += wpart[w2 * m + j];
         vtmp[j] = beta * sum;
       }
       __syncthreads();
       if (m <= kRows4Min) {
-        for (int i = k + 1 + rw; i < m; i += rnw) row_axpy(A + (int64_t)i * m, vtmp, col[i], k, m, rl);
+        for (int i = k + 1 + rw; i < m; i += rnw)
+          row_axpy_own(A + (int64_t)i * m, vtmp, col[i], k, m, rl, R, T);
       } else {
         for (int i = k + 1 + rw; i < m; i += 4 * rnw) {
           double sv[4];
@@ -1410,275 +1530,404 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
             sv[r] = ir < m ? col[ir] : 0.0;
             j1[r] = m;
           }
-          rows4_axpy(A, m, i, rnw, m, sv, j1, vtmp, k, rl);
+          rows4_axpy_own(A, m, i, rnw, m, sv, j1, vtmp, k, rl, R, T);
         }
       }
-      __syncthreads();
-      // right: all rows, columns k+1.. (warp per row)
+      if (!sync()) return fail(ST_NOCONV);
+      // right: this rank's rows, columns k+1..
       if (m <= kRows4Min) {
-        for (int i = rw; i < m; i += rnw) {
+        for (int i = gw; i < m; i += gnw) {
           double zi = row_dot(A + (int64_t)i * m, col, k + 1, m, rl);
           for (int o = 16; o > 0; o >>= 1) zi += __shfl_xor_sync(0xffffffffu, zi, o);
           row_axpy(A + (int64_t)i * m, col, zi * beta, k + 1, m, rl);
         }
       } else {
-        for (int i = rw; i < m; i += 4 * rnw) rows4_dot_axpy(A, m, i, rnw, m, col, beta, k + 1, m, rl);
+        for (int i = gw; i < m; i += 4 * gnw) rows4_dot_axpy(A, m, i, gnw, m, col, beta, k + 1, m, rl);
       }
-      __syncthreads();
     }
-    // store the reflector below the subdiagonal
-    for (int i = k + 2 + t; i < m; i += nt) A[(int64_t)i * m + k] = col[i];
-    __syncthreads();
+    // store the reflector below the subdiagonal (the rank that updated column k)
+    if (own_col(k))
+      for (int i = k + 2 + t; i < m; i += nt) A[(int64_t)i * m + k] = col[i];
+    if (!sync()) return fail(ST_NOCONV);
   }
   // ---- Hessenberg copies: Hh (inverse iteration) and the QR working copy in W ----
   double amx = 0.0;
-  for (int i = rw; i < m; i += rnw)
+  for (int i = gw; i < m; i += gnw)
     for (int j = rl; j < m; j += 32) {
       const int64_t idx = (int64_t)i * m + j;
       const double v = (j >= i - 1) ? A[idx] : 0.0;
       Hh[idx] = v;
       amx = fmax(amx, fabs(v));
     }
-  const double anorm = fmax(block_max(amx, sh.red), 1e-300);
+  amx = block_max(amx, sh.red);
+  if (t == 0) atomicMax(&ctl->anorm_bits, (unsigned long long)__double_as_longlong(amx));
+  if (!sync()) return fail(ST_NOCONV);
+  const double anorm =
+      fmax(__longlong_as_double((long long)*(volatile unsigned long long*)&ctl->anorm_bits), 1e-300);
   // the QR runs on the matrix scaled by a power of two to max |entry| in [1/2, 1)
   int gex;
   frexp(anorm, &gex);
   const double gscale = ldexp(1.0, -gex);
   const int want = pb.mode == 1 ? 1 : pb.k;
   EIG_MARK(3);
-  // ---- 4. all eigenvalues: QR in double words; FP64 if that fails ----
-  bool ok = false;
-  if (pb.fp32_locate) {
-    // a well-conditioned small problem (the Davidson projection): FP32 only locates the
-    // eigenvalues; each kept one is recomputed in FP64 by inverse iteration below
-    float* Wf = reinterpret_cast<float*>(W);
-    for (int64_t idx = t; idx < mm; idx += nt) Wf[idx] = (float)(Hh[idx] * gscale);
-    if (t == 0) sh.iscal[5] = 1;
-    __syncthreads();
-    ok = hqr_windowed<float>(Wf, m, wr, wi, anorm * gscale, dsm, sh);
-    __syncthreads();
-    for (int i = t; i < m; i += nt)
-      if (!isfinite(wr[i]) || !isfinite(wi[i])) sh.iscal[5] = 0;
-    __syncthreads();
-  }
-  if (!ok || sh.iscal[5] == 0 || !pb.fp32_locate) {
-    dw* Wd = reinterpret_cast<dw*>(W);
-    for (int64_t idx = t; idx < mm; idx += nt) Wd[idx] = dw_of_double(Hh[idx] * gscale);
-    if (t == 0) sh.iscal[5] = 1;
-    __syncthreads();
-    ok = hqr_windowed<dw>(Wd, m, wr, wi, anorm * gscale, dsm, sh);
-    __syncthreads();
-    for (int i = t; i < m; i += nt)
-      if (!isfinite(wr[i]) || !isfinite(wi[i])) sh.iscal[5] = 0;
-    __syncthreads();
-  }
-  if (!ok || sh.iscal[5] == 0) {
-#ifdef BLM_EIG_DEBUG
-    if (t == 0) printf("eig: problem %d double-word QR failed, FP64 QR\n", (int)blockIdx.x);
-#endif
-    for (int64_t idx = t; idx < mm; idx += nt) W[idx] = Hh[idx] * gscale;
-    __syncthreads();
-    ok = hqr_windowed<double>(W, m, wr, wi, anorm * gscale, dsm, sh);
-    __syncthreads();
-  }
-  if (!ok) {
-    if (t == 0) *pb.status = ST_NOCONV;
-    return;
-  }
-  for (int i = t; i < m; i += nt) {
-    wr[i] /= gscale;
-    wi[i] /= gscale;
-  }
-  __syncthreads();
-  // ---- selection of the lowest real parts; eigenvector jobs ----
-  // A job is one complex pair (both of its parts) or a run of selected real eigenvalues closer
-  // to each other than 1e-9 anorm (a numerically repeated eigenvalue): one warp computes the
-  // run's vectors one after another, each orthogonalised against the earlier ones.
-  if (t == 0) {
-    int nsel = 0;
-    for (int i = 0; i < m; ++i) vtmp[i] = 0.0;   // used flags
-    while (nsel < want) {
-      int best = -1;
-      double bv = 0.0;
-      for (int i = 0; i < m; ++i) {
-        if (vtmp[i] != 0.0) continue;
-        if (best < 0 || wr[i] < bv) {
-          best = i;
-          bv = wr[i];
-        }
-      }
-      if (best < 0) break;
-      vtmp[best] = 1.0;
-      if (wi[best] != 0.0) {
-        // the conjugate partner is adjacent (same 2 x 2 block)
-        int partner = -1;
-        if (best + 1 < m && wi[best + 1] == -wi[best] && wr[best + 1] == wr[best]) partner = best + 1;
-        if (best > 0 && wi[best - 1] == -wi[best] && wr[best - 1] == wr[best]) partner = best - 1;
-        if (partner >= 0) vtmp[partner] = 1.0;
-        const int pos = wi[best] > 0.0 ? best : (partner >= 0 ? partner : best);
-        sh.sel_idx[nsel] = pos;
-        sh.sel_part[nsel] = 1;
-        ++nsel;
-        if (nsel < want) {
-          sh.sel_idx[nsel] = pos;
-          sh.sel_part[nsel] = 2;
-          ++nsel;
-        }
-      } else {
-        sh.sel_idx[nsel] = best;
-        sh.sel_part[nsel] = 0;
-        ++nsel;
-      }
-    }
-    int njob = 0;
-    for (int q = 0; q < nsel;) {
-      int len = 1;
-      if (sh.sel_part[q] == 1) {
-        len = (q + 1 < nsel && sh.sel_part[q + 1] == 2) ? 2 : 1;
-      } else {
-        while (q + len < nsel && sh.sel_part[q + len] == 0 &&
-               wr[sh.sel_idx[q + len]] - wr[sh.sel_idx[q + len - 1]] <= 1e-9 * anorm)
-          ++len;
-      }
-      sh.job_q0[njob] = q;
-      sh.job_len[njob] = len;
-      ++njob;
-      q += len;
-    }
-    sh.iscal[2] = nsel;
-    sh.iscal[3] = njob;
-    if (pb.mode == 1 && nsel > 0 && sh.sel_part[0] != 0) sh.iscal[1] = ST_COMPLEX;
-  }
-  __syncthreads();
-  if (sh.iscal[1] != ST_OK) {
-    if (t == 0) *pb.status = sh.iscal[1];
-    return;
-  }
-  const int nsel = sh.iscal[2];
-  const int njob = sh.iscal[3];
-  EIG_MARK(4);
-  // ---- 5. eigenvectors of the Hessenberg matrix: inverse iteration, one warp per job ----
-  // The shift is the QR eigenvalue (accurate to rounding), so three solves from a fixed start
-  // vector converge; the residual ||Hh y - lambda y|| is checked before the vector is used.
+  // ---- 4. all eigenvalues, the selection of the lowest, and their eigenvectors ----
+  // With kEigLocate32 an FP32 QR only locates the eigenvalues: every kept one is recomputed in
+  // FP64 by inverse iteration (its Rayleigh quotient; a second round shifted to that quotient
+  // when the first leaves a residual above 1e-12 anorm), and the location is kept only if every
+  // kept vector converged to 1e-12 anorm, no FP64 value moved by more than 1e-4 anorm from its
+  // FP32 value, the kept eigenvalues lie below the lowest one left out by more than
+  // max(10 x the largest such move, 1e-5 anorm), no two kept entries converged to one
+  // eigenvector, and every kept complex pair keeps its imaginary part in FP64.  The output is
+  // then ordered by the FP64 values.  Otherwise (and without the flag) the double-word QR
+  // locates them (the FP64 QR if that fails) and the selection is redone.
+  bool use32 = (pb.flags & kEigLocate32) != 0;
+  int nsel = 0, njob = 0;
   const int warp = t >> 5, lane = t & 31;
-  const int nvw = min(kVecWarps, (int)((kEigSmemDoubles) / (6 * (int64_t)m)));
-  if (warp < nvw) {
-    double* cur = dsm + (int64_t)warp * 6 * m;
-    double* nxt = cur + 2 * m;
-    double* yv = nxt + 2 * m;
-    double* U = Uw + (int64_t)warp * m * (m + 1);
-    double* pl = plw + (int64_t)warp * 2 * m;
-    int* ps = psw + (int64_t)warp * m;
-    const double pert = anorm * 1e-14;   // keeps the factorisation nonsingular at an eigenvalue
-    for (int j = warp; j < njob; j += nvw) {
-      const int q0 = sh.job_q0[j], len = sh.job_len[j];
-      const bool cx = sh.sel_part[q0] != 0;
-      double sprev = NAN;
-      for (int c = 0; c < len; ++c) {
-        const int idx = sh.sel_idx[q0 + c];
-        const double lre = wr[idx], lim = cx ? wi[idx] : 0.0;
-        if (cx) {
-          warp_hess_lu<true>(Hh, m, lre + pert, lim, pert, cur, nxt, U, pl, ps);
-        } else if (!(lre == sprev)) {
-          warp_hess_lu<false>(Hh, m, lre + pert, 0.0, pert, cur, nxt, U, pl, ps);
-          sprev = lre;
+  for (;;) {
+    // the QR on rank 0; qr_ok: 1 located in FP32, 2 in double words (or FP64), 0 failed
+    if (R == 0) {
+    bool ok = false;
+    int how = 0;
+    if (use32) {
+      float* Wf = reinterpret_cast<float*>(W);
+      for (int64_t idx = t; idx < mm; idx += nt) Wf[idx] = (float)(Hh[idx] * gscale);
+      if (t == 0) sh.iscal[5] = 1;
+      __syncthreads();
+      ok = hqr_windowed<float>(Wf, m, wr, wi, anorm * gscale, dsm, sh);
+      __syncthreads();
+      for (int i = t; i < m; i += nt)
+        if (!isfinite(wr[i]) || !isfinite(wi[i])) sh.iscal[5] = 0;
+      __syncthreads();
+      if (ok && sh.iscal[5] != 0) how = 1;
+    }
+    if (how == 0) {
+      dw* Wd = reinterpret_cast<dw*>(W);
+      for (int64_t idx = t; idx < mm; idx += nt) Wd[idx] = dw_of_double(Hh[idx] * gscale);
+      if (t == 0) sh.iscal[5] = 1;
+      __syncthreads();
+      ok = hqr_windowed<dw>(Wd, m, wr, wi, anorm * gscale, dsm, sh);
+      __syncthreads();
+      for (int i = t; i < m; i += nt)
+        if (!isfinite(wr[i]) || !isfinite(wi[i])) sh.iscal[5] = 0;
+      __syncthreads();
+      if (!ok || sh.iscal[5] == 0) {
+#ifdef BLM_EIG_DEBUG
+        if (t == 0) printf("eig: problem %d double-word QR failed, FP64 QR\n", (int)blockIdx.x);
+#endif
+        for (int64_t idx = t; idx < mm; idx += nt) W[idx] = Hh[idx] * gscale;
+        __syncthreads();
+        ok = hqr_windowed<double>(W, m, wr, wi, anorm * gscale, dsm, sh);
+        __syncthreads();
+      }
+      if (ok) how = 2;
+    }
+    if (how != 0)
+      for (int i = t; i < m; i += nt) {
+        wr[i] /= gscale;
+        wi[i] /= gscale;
+      }
+    __syncthreads();
+    if (t == 0) ctl->qr_ok = how;
+    }
+    if (!sync()) return fail(ST_NOCONV);
+    {
+      const int how = *(volatile int*)&ctl->qr_ok;
+      if (how == 0) return fail(ST_NOCONV);
+      use32 = how == 1;
+    }
+    // ---- selection of the lowest real parts; eigenvector jobs ----
+    // A job is one complex pair (both of its parts) or a run of selected real eigenvalues closer
+    // to each other than 1e-9 anorm (a numerically repeated eigenvalue): one warp computes the
+    // run's vectors one after another, each orthogonalised against the earlier ones.  (FP32
+    // locations are not grouped: kept eigenvalues that close fail the check below.)
+    if (t == 0) {
+      int ns = 0;
+      for (int i = 0; i < m; ++i) vtmp[i] = 0.0;   // used flags
+      while (ns < want) {
+        int best = -1;
+        double bv = 0.0;
+        for (int i = 0; i < m; ++i) {
+          if (vtmp[i] != 0.0) continue;
+          if (best < 0 || wr[i] < bv) {
+            best = i;
+            bv = wr[i];
+          }
         }
-        for (int i = lane; i < m; i += 32) {
-          yv[i] = 1.0 + 0.1 * (double)(((i + 31 * c) * 7919) % 97) / 97.0;
-          yv[m + i] = 0.0;
+        if (best < 0) break;
+        vtmp[best] = 1.0;
+        if (wi[best] != 0.0) {
+          // the conjugate partner is adjacent (same 2 x 2 block)
+          int partner = -1;
+          if (best + 1 < m && wi[best + 1] == -wi[best] && wr[best + 1] == wr[best]) partner = best + 1;
+          if (best > 0 && wi[best - 1] == -wi[best] && wr[best - 1] == wr[best]) partner = best - 1;
+          if (partner >= 0) vtmp[partner] = 1.0;
+          const int pos = wi[best] > 0.0 ? best : (partner >= 0 ? partner : best);
+          sh.sel_idx[ns] = pos;
+          sh.sel_part[ns] = 1;
+          ++ns;
+          if (ns < want) {
+            sh.sel_idx[ns] = pos;
+            sh.sel_part[ns] = 2;
+            ++ns;
+          }
+        } else {
+          sh.sel_idx[ns] = best;
+          sh.sel_part[ns] = 0;
+          ++ns;
         }
-        __syncwarp();
-        for (int it = 0; it < 3; ++it) {
-          if (cx) {
-            warp_hess_solve<true>(m, pert, U, pl, ps, yv);
-          } else {
-            warp_hess_solve<false>(m, pert, U, pl, ps, yv);
-            // orthogonalise against the run's earlier vectors (unit norm, stored in cvec)
-            for (int e = 0; e < c; ++e) {
-              const double* ve = cvec + (int64_t)(q0 + e) * 2 * m;
-              const double d = warp_dot(ve, yv, m);
-              for (int i = lane; i < m; i += 32) yv[i] -= d * ve[i];
+      }
+      double lo_out = INFINITY;   // the lowest real part left out
+      for (int i = 0; i < m; ++i)
+        if (vtmp[i] == 0.0 && wr[i] < lo_out) lo_out = wr[i];
+      sh.scal[3] = lo_out;
+      const double run_gap = use32 ? 0.0 : 1e-9 * anorm;
+      int nj = 0;
+      for (int q = 0; q < ns;) {
+        int len = 1;
+        if (sh.sel_part[q] == 1) {
+          len = (q + 1 < ns && sh.sel_part[q + 1] == 2) ? 2 : 1;
+        } else {
+          while (q + len < ns && sh.sel_part[q + len] == 0 &&
+                 wr[sh.sel_idx[q + len]] - wr[sh.sel_idx[q + len - 1]] <= run_gap)
+            ++len;
+        }
+        sh.job_q0[nj] = q;
+        sh.job_len[nj] = len;
+        ++nj;
+        q += len;
+      }
+      sh.iscal[2] = ns;
+      sh.iscal[3] = nj;
+      for (int q = 0; q < ns; ++q) sh.out_pos[q] = q;
+      if (pb.mode == 1 && ns > 0 && sh.sel_part[0] != 0 && !use32) sh.iscal[1] = ST_COMPLEX;
+    }
+    __syncthreads();
+    if (sh.iscal[1] != ST_OK) {
+      if (t == 0) *pb.status = sh.iscal[1];
+      return;
+    }
+    nsel = sh.iscal[2];
+    njob = sh.iscal[3];
+    EIG_MARK(4);
+    // ---- 5. eigenvectors of the Hessenberg matrix: inverse iteration, one warp per job ----
+    // The shift is the located eigenvalue, so three solves from a fixed start vector converge;
+    // the residual ||Hh y - lambda y|| is checked before the vector is used.
+    // (the team's vector warps share the kVecWarps factor slots: global vector warp gv)
+    const int nvw = min(max(1, kVecWarps / T), (int)((kEigSmemDoubles) / (6 * (int64_t)m)));
+    const int gv = R * nvw + warp, gnv = T * nvw;
+    if (warp < nvw) {
+      double* cur = dsm + (int64_t)warp * 6 * m;
+      double* nxt = cur + 2 * m;
+      double* yv = nxt + 2 * m;
+      double* U = Uw + (int64_t)gv * m * (m + 1);
+      double* pl = plw + (int64_t)gv * 2 * m;
+      int* ps = psw + (int64_t)gv * m;
+      const double pert = anorm * 1e-14;   // keeps the factorisation nonsingular at an eigenvalue
+      for (int j = gv; j < njob; j += gnv) {
+        const int q0 = sh.job_q0[j], len = sh.job_len[j];
+        const bool cx = sh.sel_part[q0] != 0;
+        double sprev = NAN;
+        for (int c = 0; c < len; ++c) {
+          const int idx = sh.sel_idx[q0 + c];
+          const double lre = wr[idx], lim = cx ? wi[idx] : 0.0;
+          // An FP32 location gets a second round, shifted to the first round's Rayleigh
+          // quotient, when the first leaves a residual above 1e-12 anorm (a neighbour closer
+          // than the FP32 error allows slows the first round's convergence).
+          double sre = lre, sim = lim, qre = 0.0, qim = 0.0, res = INFINITY;
+          const int rounds = use32 ? 2 : 1;
+          for (int round = 0; round < rounds; ++round) {
+            if (round == 1) {
+              if (res <= 1e-12 * anorm) break;
+              sre = qre;
+              sim = cx ? qim : 0.0;
+              sprev = NAN;
+            }
+            if (cx) {
+              warp_hess_lu<true>(Hh, m, sre + pert, sim, pert, cur, nxt, U, pl, ps);
+            } else if (!(sre == sprev)) {
+              warp_hess_lu<false>(Hh, m, sre + pert, 0.0, pert, cur, nxt, U, pl, ps);
+              sprev = sre;
+            }
+            if (round == 0) {
+              for (int i = lane; i < m; i += 32) {
+                yv[i] = 1.0 + 0.1 * (double)(((i + 31 * c) * 7919) % 97) / 97.0;
+                yv[m + i] = 0.0;
+              }
               __syncwarp();
             }
+            for (int it = 0; it < (round == 0 ? 3 : 2); ++it) {
+              if (cx) {
+                warp_hess_solve<true>(m, pert, U, pl, ps, yv);
+              } else {
+                warp_hess_solve<false>(m, pert, U, pl, ps, yv);
+                // orthogonalise against the run's earlier vectors (unit norm, stored in cvec)
+                for (int e = 0; e < c; ++e) {
+                  const double* ve = cvec + (int64_t)(q0 + e) * 2 * m;
+                  const double d = warp_dot(ve, yv, m);
+                  for (int i = lane; i < m; i += 32) yv[i] -= d * ve[i];
+                  __syncwarp();
+                }
+              }
+            }
+            // normalise; H y into cur (re | im); the Rayleigh quotient y^H H y / y^H y becomes
+            // the eigenvalue (FP64 accurate whatever the QR's precision); then the residual
+            double nrm = 0.0;
+            for (int i = lane; i < m; i += 32) nrm += yv[i] * yv[i] + (cx ? yv[m + i] * yv[m + i] : 0.0);
+            nrm = sqrt(warp_sum(nrm));
+            const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+            for (int i = lane; i < 2 * m; i += 32) yv[i] = (i < m || cx) ? yv[i] * inv : 0.0;
+            __syncwarp();
+            for (int i = 0; i < m; ++i) {
+              const double* hrow = Hh + (int64_t)i * m;
+              double hr = 0.0, hm = 0.0;
+              for (int k2 = (i > 0 ? i - 1 : 0) + lane; k2 < m; k2 += 32) {
+                hr = fma(hrow[k2], yv[k2], hr);
+                if (cx) hm = fma(hrow[k2], yv[m + k2], hm);
+              }
+              hr = warp_sum(hr);
+              if (cx) hm = warp_sum(hm);
+              if (lane == 0) {
+                cur[i] = hr;
+                cur[m + i] = hm;
+              }
+            }
+            __syncwarp();
+            qre = 0.0;
+            qim = 0.0;
+            for (int i = lane; i < m; i += 32) {
+              qre += yv[i] * cur[i] + (cx ? yv[m + i] * cur[m + i] : 0.0);
+              if (cx) qim += yv[i] * cur[m + i] - yv[m + i] * cur[i];
+            }
+            qre = warp_sum(qre);   // y is unit: y^H y = 1
+            qim = cx ? warp_sum(qim) : 0.0;
+            double rr = 0.0;
+            for (int i = lane; i < m; i += 32) {
+              const double er = cur[i] - (qre * yv[i] - qim * yv[m + i]);
+              const double ei = cx ? cur[m + i] - (qre * yv[m + i] + qim * yv[i]) : 0.0;
+              rr += er * er + ei * ei;
+            }
+            res = sqrt(warp_sum(rr));
           }
-        }
-        // normalise; H y into cur (re | im); the Rayleigh quotient y^H H y / y^H y becomes the
-        // eigenvalue (FP64 accurate whatever the QR's precision); then the residual
-        double nrm = 0.0;
-        for (int i = lane; i < m; i += 32) nrm += yv[i] * yv[i] + (cx ? yv[m + i] * yv[m + i] : 0.0);
-        nrm = sqrt(warp_sum(nrm));
-        const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
-        for (int i = lane; i < 2 * m; i += 32) yv[i] = (i < m || cx) ? yv[i] * inv : 0.0;
-        __syncwarp();
-        for (int i = 0; i < m; ++i) {
-          const double* hrow = Hh + (int64_t)i * m;
-          double hr = 0.0, hm = 0.0;
-          for (int k2 = (i > 0 ? i - 1 : 0) + lane; k2 < m; k2 += 32) {
-            hr = fma(hrow[k2], yv[k2], hr);
-            if (cx) hm = fma(hrow[k2], yv[m + k2], hm);
-          }
-          hr = warp_sum(hr);
-          if (cx) hm = warp_sum(hm);
           if (lane == 0) {
-            cur[i] = hr;
-            cur[m + i] = hm;
-          }
-        }
-        __syncwarp();
-        double qre = 0.0, qim = 0.0;
-        for (int i = lane; i < m; i += 32) {
-          qre += yv[i] * cur[i] + (cx ? yv[m + i] * cur[m + i] : 0.0);
-          if (cx) qim += yv[i] * cur[m + i] - yv[m + i] * cur[i];
-        }
-        qre = warp_sum(qre);   // y is unit: y^H y = 1
-        qim = cx ? warp_sum(qim) : 0.0;
-        double rr = 0.0;
-        for (int i = lane; i < m; i += 32) {
-          const double er = cur[i] - (qre * yv[i] - qim * yv[m + i]);
-          const double ei = cx ? cur[m + i] - (qre * yv[m + i] + qim * yv[i]) : 0.0;
-          rr += er * er + ei * ei;
-        }
-        rr = warp_sum(rr);
-        // A converged vector (residual <= 1e-9 ||H||, quotient next to the QR value) gives the
-        // eigenvalue as its Rayleigh quotient; otherwise the QR value stands (a nearly defective
-        // eigenvalue converges slowly under inverse iteration).  Only a vector that is no
-        // eigenvector at all (residual above 1e-6 ||H||) fails the solve.
-        if (lane == 0) {
-          const double res = sqrt(rr);
-          if (!(res <= 1e-6 * anorm)) sh.iscal[4] = 1;
-          if (res <= 1e-9 * anorm && fabs(qre - lre) <= 1e-6 * anorm) wr[idx] = qre;
+            const bool conv = res <= (use32 ? 1e-12 : 1e-9) * anorm;
+            if (use32) {
+              // an FP32 location must give a converged vector whose quotient stays near it
+              const double mv = fabs(qre - lre);
+              const double e = (conv && mv <= 1e-4 * anorm) ? mv : INFINITY;
+              ctl->sel_err[q0 + c] = e;
+              ctl->sel_qim[q0 + c] = qim;
+              if (cx && c == 0 && len == 2) {
+                ctl->sel_err[q0 + 1] = e;
+                ctl->sel_qim[q0 + 1] = qim;
+              }
+              if (e != INFINITY) wr[idx] = qre;
+            } else {
+              // A converged vector (residual <= 1e-9 ||H||, quotient next to the QR value) gives
+              // the eigenvalue as its Rayleigh quotient; otherwise the QR value stands (a nearly
+              // defective eigenvalue converges slowly under inverse iteration).  Only a vector
+              // that is no eigenvector at all (residual above 1e-6 ||H||) fails the solve.
+              if (!(res <= 1e-6 * anorm)) ctl->vec_fail = 1;
+              if (conv && fabs(qre - lre) <= 1e-6 * anorm) wr[idx] = qre;
+            }
 #ifdef BLM_EIG_DEBUG
-          if (!(res <= 1e-9 * anorm) || !(fabs(qre - lre) <= 1e-6 * anorm))
-            printf("eig: problem %d eigenvector %d residual %.3e shift %.15g quotient %.15g (anorm %.3e)\n",
-                   (int)blockIdx.x, q0 + c, res, lre, qre, anorm);
+            if (!conv || !(fabs(qre - lre) <= 1e-6 * anorm))
+              printf("eig: problem %d eigenvector %d residual %.3e shift %.15g quotient %.15g (anorm %.3e)%s\n",
+                     (int)blockIdx.x, q0 + c, res, lre, qre, anorm, use32 ? " [fp32 location]" : "");
 #endif
+          }
+          double* dst = cvec + (int64_t)(q0 + c) * 2 * m;
+          for (int i = lane; i < 2 * m; i += 32) dst[i] = yv[i];
+          if (cx && c == 0 && len == 2) {
+            double* dst2 = cvec + (int64_t)(q0 + 1) * 2 * m;
+            for (int i = lane; i < 2 * m; i += 32) dst2[i] = yv[i];
+          }
+          __syncwarp();
+          if (cx) break;   // the pair's second entry shares the vector
         }
-        double* dst = cvec + (int64_t)(q0 + c) * 2 * m;
-        for (int i = lane; i < 2 * m; i += 32) dst[i] = yv[i];
-        if (cx && c == 0 && len == 2) {
-          double* dst2 = cvec + (int64_t)(q0 + 1) * 2 * m;
-          for (int i = lane; i < 2 * m; i += 32) dst2[i] = yv[i];
-        }
-        __syncwarp();
-        if (cx) break;   // the pair's second entry shares the vector
       }
     }
+    if (!sync()) return fail(ST_NOCONV);
+    if (!use32) break;
+    // ---- is the FP32 location good enough? (every rank decides alike) ----
+    if (t == 0) {
+      double mv = 0.0, top = -INFINITY;
+      for (int q = 0; q < nsel; ++q) {
+        mv = fmax(mv, *(volatile double*)&ctl->sel_err[q]);   // INFINITY for a failed vector
+        top = fmax(top, wr[sh.sel_idx[q]]);
+      }
+      const double sep = fmax(10.0 * mv, 1e-5 * anorm);
+      // membership: the kept eigenvalues must lie clearly below the first one left out
+      bool good = mv <= 1e-4 * anorm && !(sh.scal[3] - top <= sep);
+      for (int q = 0; q < nsel && good; ++q) {
+        const int iq = sh.sel_idx[q];
+        // a pair must stay a pair: the FP64 quotient's imaginary part agrees with the FP32 one
+        // (two close real eigenvalues located as a pair give a real quotient)
+        if (sh.sel_part[q] != 0) {
+          const double qi = *(volatile double*)&ctl->sel_qim[q];
+          if (!(fabs(qi) > 10.0 * fabs(qi - wi[iq]) && fabs(qi) > 1e-9 * anorm)) good = false;
+        }
+        if (pb.mode == 1 && q == 0 && sh.sel_part[q] != 0) good = false;   // must be real
+        // two kept entries whose vectors converged to one eigenvector
+        for (int r = q + 1; r < nsel && good; ++r) {
+          const int ir = sh.sel_idx[r];
+          if (ir != iq && fabs(wr[ir] - wr[iq]) <= 1e-9 * anorm) good = false;
+        }
+      }
+      // a pair cut by N_K (its real part kept alone) must stay the highest kept eigenvalue
+      if (good && nsel > 0 && sh.sel_part[nsel - 1] == 1) {
+        const double vp = wr[sh.sel_idx[nsel - 1]];
+        for (int q = 0; q < nsel - 1 && good; ++q)
+          if (sh.sel_idx[q] != sh.sel_idx[nsel - 1] && !(wr[sh.sel_idx[q]] < vp - sep)) good = false;
+      }
+      // output in ascending order of the FP64 values (a pair's two entries stay together)
+      if (good) {
+        int pos = 0;
+        bool placed[kMaxKeep];
+        for (int q = 0; q < nsel; ++q) placed[q] = false;
+        for (;;) {
+          int bq = -1;
+          for (int q = 0; q < nsel; ++q) {
+            if (placed[q] || sh.sel_part[q] == 2) continue;
+            if (bq < 0 || wr[sh.sel_idx[q]] < wr[sh.sel_idx[bq]]) bq = q;
+          }
+          if (bq < 0) break;
+          placed[bq] = true;
+          sh.out_pos[bq] = pos++;
+          if (sh.sel_part[bq] == 1 && bq + 1 < nsel && sh.sel_part[bq + 1] == 2) {
+            placed[bq + 1] = true;
+            sh.out_pos[bq + 1] = pos++;
+          }
+        }
+      }
+      sh.iscal[6] = good ? 1 : 0;
+#ifdef BLM_EIG_DEBUG
+      if (!good && R == 0)
+        printf("eig: problem %d (m %d) FP32 location rejected: max move %.3e, gap to the first left "
+               "out %.3e, separation needed %.3e (anorm %.3e); kept:\n",
+               (int)blockIdx.x, m, mv, sh.scal[3] - top, sep, anorm);
+      if (!good && R == 0)
+        for (int q = 0; q < nsel; ++q)
+          printf("  entry %d idx %d part %d re %.15g im %.3e err %.3e\n", q, sh.sel_idx[q],
+                 sh.sel_part[q], wr[sh.sel_idx[q]], wi[sh.sel_idx[q]], ctl->sel_err[q]);
+#endif
+    }
+    __syncthreads();
+    if (sh.iscal[6]) break;
+    use32 = false;   // locate again with double words
+    if (!sync()) return fail(ST_NOCONV);   // (every rank has read wr before the QR rewrites it)
   }
   // Householder vectors as rows for coalesced per-warp back-transformation (W is free now)
-  for (int k = rw; k < m; k += rnw)
+  for (int k = gw; k < m; k += gnw)
     for (int i = rl; i < m; i += 32)
       W[(int64_t)k * m + i] = (i >= k + 2 && k < m - 2) ? A[(int64_t)i * m + k] : 0.0;
-  __syncthreads();
-  if (sh.iscal[4] != 0) {
-    if (t == 0) *pb.status = ST_NOCONV;
-    return;
-  }
+  if (!sync()) return fail(ST_NOCONV);
+  if (*(volatile int*)&ctl->vec_fail != 0) return fail(ST_NOCONV);
   EIG_MARK(5);
   // ---- 6. back-transformation v = D L^-T Q y, one warp per selected direction ----
   // A complex eigenvector is rotated so that its largest-magnitude component is real and
   // positive; its real part (kept alone when N_K ends inside the pair) is then well defined.
   const int nw = min(nt >> 5, (int)(kEigSmemDoubles / (2 * (int64_t)m)));
-  for (int q = warp; q < nsel && warp < nw; q += nw) {
+  for (int q = R * nw + warp; q < nsel && warp < nw; q += T * nw) {
     const int part = sh.sel_part[q];
     double* vr2 = dsm + (int64_t)warp * 2 * m;
     double* vi2 = vr2 + m;
@@ -1718,17 +1967,18 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh) {
       }
       __syncwarp();
     }
-    double* out = pb.vec + (int64_t)q * m;
+    const int op = sh.out_pos[q];
+    double* out = pb.vec + (int64_t)op * m;
     const double* res = (part == 2) ? vi2 : vr2;
     for (int i = lane; i < m; i += 32) out[i] = res[i];
-    if (lane == 0) pb.lam[q] = wr[sh.sel_idx[q]];
+    if (lane == 0) pb.lam[op] = wr[sh.sel_idx[q]];
     __syncwarp();
   }
-  __syncthreads();
-  if (t == 0) *pb.status = (nsel == (pb.mode == 1 ? 1 : pb.k)) ? ST_OK : ST_NOCONV;
+  if (!sync()) return fail(ST_NOCONV);
+  if (t == 0 && R == 0) *pb.status = (nsel == (pb.mode == 1 ? 1 : pb.k)) ? ST_OK : ST_NOCONV;
   EIG_MARK(6);
 #ifdef BLM_EIG_TIMING
-  if (t == 0 && blockIdx.x == 0)
+  if (t == 0 && R == 0 && blockIdx.x == 0)
     printf("eig timing m=%d: scale %lld chol+std %lld hess %lld qr %lld vec %lld back %lld cycles\n",
            m, tmark[1] - tmark[0], tmark[2] - tmark[1], tmark[3] - tmark[2], tmark[4] - tmark[3],
            tmark[5] - tmark[4], tmark[6] - tmark[5]);
@@ -1744,13 +1994,32 @@ eig_kernel(const EigProblem* __restrict__ probs) {
   dense_geig(pb, dsm, sh);
 }
 
+// CTA c of a team launch solves problem prob[c] as rank rank[c] of size[c] CTAs.
+constexpr int kTeamGridMax = 160;
+struct TeamMap {
+  uint16_t prob[kTeamGridMax];
+  uint8_t rank[kTeamGridMax];
+  uint8_t size[kTeamGridMax];
+};
+
+__global__ void __launch_bounds__(kEigThreads)
+eig_team_kernel(const EigProblem* __restrict__ probs, TeamCtl* ctl, const __grid_constant__ TeamMap map) {
+  extern __shared__ double dsm[];
+  __shared__ Shared sh;
+  const int p = map.prob[blockIdx.x];
+  const EigProblem pb = probs[p];
+  if (pb.run_if_noconv && *pb.run_if_noconv != ST_NOCONV) return;
+  dense_geig(pb, dsm, sh, Team{(int)map.rank[blockIdx.x], (int)map.size[blockIdx.x], ctl + p});
+}
+
 // ---------------------------------------------------------------------------------------------
 // Generalized Davidson for the lowest eigenpair of H c = lambda S c (the combined problem of
 // Eq. 7 when it is too large for the dense QR on one SM).  The basis V is kept S-orthonormal, so
 // the projected problem V^T H V y = theta y is a small standard eigenproblem (solved with the
 // dense routine above); the Ritz pair with the lowest real part is expanded with the diagonal
 // preconditioner t = -(diag H - theta diag S)^-1 r, starting from the Psi direction e_0.
-// Converged when ||H u - theta S u|| <= tol * ||S u|| * max(1, |theta|).
+// Converged when ||H u - theta S u|| <= tol * ||S u|| * max(1, |theta|), or when that ratio has
+// stayed within 100 tol for six iterations without halving (the rounding floor).
 // ---------------------------------------------------------------------------------------------
 constexpr int kDavMax = 40;
 
@@ -1922,6 +2191,8 @@ davidson_kernel(const EigProblem* __restrict__ probs, double tol, int max_iter, 
   bool fresh = true;      // projected matrix must be rebuilt (start, restart)
   double theta = 0.0;
   int status = ST_NOCONV;
+  double best_rel = INFINITY;
+  int since_best = 0;
 #ifdef BLM_EIG_TIMING
   long long dt[5] = {0, 0, 0, 0, 0}, dc0 = clock64();
   int dits = 0;
@@ -1968,7 +2239,8 @@ davidson_kernel(const EigProblem* __restrict__ probs, double tol, int max_iter, 
     if (t == 0) *sStat = ST_OK;
     __syncthreads();
     DAV_T(0);
-    EigProblem sp{k, 1, 0, 1, sS, sH, sW, sLam, sVec, sStat};
+    // (double-word location: the Ritz pair must be accurate to the Davidson tolerance)
+    EigProblem sp{k, 1, 0, kEigUnitS, sS, sH, sW, sLam, sVec, sStat};
     dense_geig(sp, dsm, sh);
     __syncthreads();
     DAV_T(1);
@@ -1995,7 +2267,17 @@ davidson_kernel(const EigProblem* __restrict__ probs, double tol, int max_iter, 
     const double rn = sqrt(dotv(r, r, m, sh));
     const double sn = sqrt(dotv(Su, Su, m, sh));
     DAV_T(2);
-    if (rn <= tol * sn * fmax(1.0, fabs(theta))) {
+    // Converged at tol; or, where rounding keeps the residual from reaching tol (its floor is
+    // about m eps ||H|| ||u||), once it has stayed within 100 tol for six iterations without
+    // halving.
+    const double rel = rn / (sn * fmax(1.0, fabs(theta)));
+    if (rel < 0.5 * best_rel) {
+      best_rel = rel;
+      since_best = 0;
+    } else {
+      ++since_best;
+    }
+    if (rel <= tol || (best_rel <= 100.0 * tol && since_best >= 6)) {
       status = ST_OK;
       break;
     }
@@ -2115,12 +2397,75 @@ cudaError_t launch_davidson(const EigProblem* probs, double tol, int max_iter, d
   return cudaLaunchKernelEx(&cfg, davidson_kernel, probs, tol, max_iter, ctl);
 }
 
-void launch_eig(const EigProblem* probs, int nprob, int threads, cudaStream_t st) {
+size_t eig_team_ctl_bytes(int nprob) { return sizeof(TeamCtl) * (size_t)(nprob > 0 ? nprob : 0); }
+
+// CTAs per problem.  The estimated time of a problem of dimension d on T CTAs is
+// d^3 (5 / T + 1): the FP64 reductions and eigenvectors (about 5 d^3 cycles on one CTA) are
+// shared out, the QR (about d^3 with the FP32 location) is not.  Starting from one CTA each,
+// the slowest problems get one more CTA together while the SMs last.
+static std::vector<int> team_sizes(const int32_t* dims, int nprob, int sms) {
+  std::vector<int> T(nprob, 1);
+  auto est = [&](int p) { const double d = dims[p]; return d * d * d * (5.0 / T[p] + 1.0); };
+  int budget = sms - nprob;
+  while (budget > 0) {
+    double mx = 0.0;
+    for (int p = 0; p < nprob; ++p) mx = std::max(mx, est(p));
+    std::vector<int> top;
+    for (int p = 0; p < nprob; ++p)
+      if (est(p) >= 0.98 * mx) top.push_back(p);
+    bool can = (int)top.size() <= budget;
+    for (int p : top) can = can && T[p] < kMaxTeam && dims[p] > kRows4Min;
+    if (!can) break;
+    for (int p : top) ++T[p];
+    budget -= (int)top.size();
+  }
+  return T;
+}
+
+void launch_eig(const EigProblem* probs, int nprob, int threads, cudaStream_t st, const int32_t* dims,
+                void* team_ctl) {
   if (nprob <= 0) return;
   (void)threads;
   const int smem = 200 * 1024;
-  cudaFuncSetAttribute(eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  eig_kernel<<<nprob, kEigThreads, smem, st>>>(probs);
+  static int sms = 0;
+  if (sms == 0) {
+    cudaFuncSetAttribute(eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(eig_team_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int dev = 0, n = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eig_team_kernel, kEigThreads, smem);
+    sms = std::min(n * std::max(per_sm, 1), kTeamGridMax);
+  }
+  std::vector<int> T;
+  if (dims != nullptr && team_ctl != nullptr && nprob < sms) T = team_sizes(dims, nprob, sms);
+  int grid = 0;
+  for (int v : T) grid += v;
+  if (grid <= nprob) {
+    eig_kernel<<<nprob, kEigThreads, smem, st>>>(probs);
+    return;
+  }
+  TeamMap map = {};
+  for (int p = 0, c = 0; p < nprob; ++p)
+    for (int r = 0; r < T[p]; ++r, ++c) {
+      map.prob[c] = (uint16_t)p;
+      map.rank[c] = (uint8_t)r;
+      map.size[c] = (uint8_t)T[p];
+    }
+  if (cudaMemsetAsync(team_ctl, 0, eig_team_ctl_bytes(nprob), st) != cudaSuccess) return;
+  // a cooperative launch (every CTA resident: the team barriers need it), in the
+  // launch-attribute form that stream capture accepts
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kEigThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, eig_team_kernel, probs, reinterpret_cast<TeamCtl*>(team_ctl), map);
 }
 
 }  // namespace blm
@@ -2159,7 +2504,7 @@ noalloc_block_kernel(double* scratch, const double* S, const double* H, int dim,
   int32_t* status = reinterpret_cast<int32_t*>(vec + (size_t)kNoAllocMaxKeep * kNoAllocMaxDim);
   if (threadIdx.x == 0) *status = ST_OK;     // the array keeps the previous call's contents
   __syncthreads();
-  EigProblem pb{dim, keep, 0, 0, S, H, work, lambda, vec, status};
+  EigProblem pb{dim, keep, 0, kEigLocate32, S, H, work, lambda, vec, status};
   dense_geig(pb, dsm, sh);
   __syncthreads();
   if (*status != ST_OK) return;

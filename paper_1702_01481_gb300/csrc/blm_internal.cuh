@@ -184,7 +184,7 @@ struct EigProblem {
   int32_t m;           // dimension (1 + tangent)
   int32_t k;           // directions wanted (lowest real parts)
   int32_t mode;        // 0: block (complex pair -> Re, Im), 1: combined (lowest must be real)
-  int32_t fp32_locate; // 1: locate eigenvalues with an FP32 QR (well-conditioned small problems)
+  int32_t flags;       // kEigLocate32 | kEigUnitS (below)
   const double* S;     // m x m row-major
   const double* H;     // m x m row-major
   double* work;        // 5 m^2 + 16 m doubles
@@ -194,7 +194,19 @@ struct EigProblem {
   const int32_t* run_if_noconv;  // if set: solve only when *run_if_noconv == ST_NOCONV (the
                                  // dense fallback after a Davidson run, decided on the device)
 };
-void launch_eig(const EigProblem* probs, int nprob, int threads, cudaStream_t st);
+// EigProblem::flags.  kEigLocate32: an FP32 QR locates the eigenvalues and FP64 inverse
+// iteration recomputes the kept ones; the double-word QR runs only when that location cannot be
+// trusted (a kept vector that does not converge, or kept eigenvalues closer to each other or to
+// the first one left out than the FP32 values can resolve).  kEigUnitS: S is the identity (the
+// Davidson projection's S-orthonormal basis), so the Cholesky reduction is skipped.
+constexpr int32_t kEigLocate32 = 1;
+constexpr int32_t kEigUnitS = 2;
+// Launches the dense solver on nprob problems.  With their dimensions (host) and a control
+// buffer (device, eig_team_ctl_bytes(nprob)) the largest problems are solved by teams of CTAs
+// of one cooperative launch; otherwise one CTA per problem.
+void launch_eig(const EigProblem* probs, int nprob, int threads, cudaStream_t st,
+                const int32_t* dims = nullptr, void* team_ctl = nullptr);
+size_t eig_team_ctl_bytes(int nprob);
 size_t eig_work_doubles(int64_t m);
 // Lowest eigenpair by generalized Davidson (k = 1, mode 1) of the one problem *probs, whose
 // workspace `work` (device, davidson_work_doubles(m) doubles) and dimension m the caller passes
