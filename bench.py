@@ -267,10 +267,25 @@ def run_ours(args, rank, world):
         ach = flop / (kms / klaunch / 1e3) / 1e12
         peak = 1.7 * 2 * 152 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 3), "unit": "TFLOP/s",
-                "frac": round(ach / peak, 4), "traffic": None, "kernel": "eig_kernel (FP64 block solves)",
+                "frac": round(ach / peak, 4), "traffic": None,
+                "kernel": "eig_team_kernel (block solves: FP64 reductions on teams of CTAs, FP32 QR)",
                 "per_launch_algorithmic_flop": flop,
-                "note": "FP64 latency bound: one CTA per block, serial QR chase; peak = measured "
+                "note": "latency bound (serial QR chase, per-column barriers); peak = measured "
                         "FP64 FMA rate x 2 x 152 SMs x max clock"}
+    elif kname in ("operand_prep_pass1", "operand_prep_pass2") and klaunch and mixed:
+        # HBM: per sample the pass reads its two FP32 source rows (O, G of n values; p, r of dc
+        # in the second sweep) and writes the hi | lo operand rows of the A and B arrays
+        # (4 bytes per value for BF16X4, 8 for TF32X4)
+        width = n if kname.endswith("1") else sum(wl.n_keep for _ in range(len(offs) - 1))
+        opb = 8 if args.precision == "tf32x4" else 4
+        per_sample = 2 * width * 4 + 2 * width * opb
+        per_launch = per_sample * ns * res["steps"] / klaunch
+        ach = per_launch / (kms / klaunch / 1e3) / 1e9
+        p = pk.get("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": p, "unit": "GB/s",
+                "frac": round(ach / p, 4), "traffic": None,
+                "kernel": "prep_direct_kernel (%s)" % kname, "per_launch_algorithmic_bytes": per_launch,
+                "peak_source": "measured" if "hbm_gbs" in pk else "fallback"}
     elif klaunch:
         roof = {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
                 "traffic": None, "kernel": kname, "note": "no roofline model for this kernel class"}

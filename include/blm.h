@@ -241,7 +241,7 @@ blm_status blm_set_wait_limit(blm_handle* h, uint32_t polls);
  * launches, per kernel class.  blm_profile_read synchronises the stream and fills, for classes
  * 0 .. n-1 (n <= BLM_PROF_CLASSES), the summed device milliseconds and launch counts since the
  * last reset (enable != 0 also resets).  blm_profile_class_name(i) names class i. */
-#define BLM_PROF_CLASSES 13
+#define BLM_PROF_CLASSES 14
 blm_status blm_profile(blm_handle* h, int enable);
 blm_status blm_profile_read(blm_handle* h, int n, double* ms, int64_t* launches);
 const char* blm_profile_class_name(int i);

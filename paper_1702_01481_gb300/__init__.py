@@ -82,7 +82,7 @@ _sig = {
     "blm_block_solve_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P,
                                                ctypes.c_void_p]),
 }
-BLM_PROF_CLASSES = 13
+BLM_PROF_CLASSES = 14
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
     _f.restype = _res

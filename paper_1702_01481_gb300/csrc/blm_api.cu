@@ -32,13 +32,15 @@ constexpr double kDavidsonTol = 1e-13;
 constexpr int kDavidsonIter = 400;
 
 struct Alloc {
-  // sizes in bytes of every device buffer; filled by plan()
+  // offsets in bytes of every device buffer in the handle's one allocation; filled by plan().
+  // Buffers of 64 MiB and more start on 2 MiB boundaries (the large-page size), the rest on 256 B.
   size_t total = 0;
   std::vector<std::pair<void**, size_t>> items;
   void add(void** p, size_t bytes) {
-    bytes = (bytes + 255) / 256 * 256;
-    items.emplace_back(p, bytes);
-    total += bytes;
+    const size_t align = bytes >= ((size_t)64 << 20) ? ((size_t)2 << 20) : 256;
+    total = (total + align - 1) / align * align;
+    items.emplace_back(p, total);
+    total += (bytes + 255) / 256 * 256;
   }
 };
 
@@ -188,12 +190,12 @@ namespace {
 enum ProfClass {
   PC_SHIFT = 0, PC_SUMS = 1, PC_CONTRACT = 2, PC_TC1 = 3, PC_HIST = 4, PC_ASSEMBLE = 5,
   PC_EIG_BLOCKS = 6, PC_DIRS = 7, PC_PROJECT = 8, PC_TC2 = 9, PC_EIG_COMBINED = 10, PC_UPDATE = 11,
-  PC_PREP = 12
+  PC_PREP = 12, PC_PREP2 = 13
 };
 const char* kProfNames[BLM_PROF_CLASSES] = {
     "reference_shift", "first_moments", "contract_f64", "contract_tc_pass1", "history_terms",
     "assemble", "eig_blocks", "directions", "project", "contract_tc_pass2", "eig_combined",
-    "update", "operand_prep"};
+    "update", "operand_prep_pass1", "operand_prep_pass2"};
 
 cudaEvent_t pool_event(blm_handle* h) {
   if (!h->ev_pool.empty()) {
@@ -637,7 +639,7 @@ blm_status project_dev(blm_handle* h, const T* O, const T* G, const T* E, const 
                                        h->d_cen, PY, PZ, dc, cnt, h->maxM, h->maxK, st);
       }
       {
-        Prof pr(h, PC_PREP);
+        Prof pr(h, PC_PREP2);
         launch_prep(PY, PZ, Es, ws, cnt, dc, dc, nullptr, h->d_opA, h->d_opBS, h->d_opBH,
                     h->op_row_bytes, h->d_cvec, h->d_cvec + dc, h->d_cvec + 2 * dc, nullptr, tf,
                     st);
@@ -949,11 +951,7 @@ blm_status blm_create(const blm_problem* p, void* stream, blm_handle** out) {
     delete h;
     return BLM_ERR_NOMEM;
   }
-  char* cur = (char*)h->base;
-  for (auto& it : a.items) {
-    *it.first = cur;
-    cur += it.second;
-  }
+  for (auto& it : a.items) *it.first = (char*)h->base + it.second;
   blm_status s = BLM_OK;
   // history directions
   if (h->n_old > 0) {

@@ -235,6 +235,9 @@ struct Shared {
   int job_q0[kMaxKeep];     // eigenvector jobs: selection entries [job_q0, job_q0 + job_len)
   int job_len[kMaxKeep];
   int out_pos[kMaxKeep];    // output position of each selection entry (ascending eigenvalues)
+#ifdef BLM_EIG_TIMING
+  long long msub[4];        // multi-bulge sweeps: window loads, chase, write-back, outside
+#endif
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -452,6 +455,31 @@ struct QrArith<dw> {
 // Rows above and columns right of the window receive the same operations afterwards from the
 // stored reflectors, all bulges of one time step on a sliding run of 3 kNbMax entries (their
 // ranges are disjoint and adjacent), time steps in order.
+// The w x w window at (a, a) of G into shared memory, eight loads in flight per thread.
+template <typename R>
+__device__ __forceinline__ void load_window(const R* G, int m, int a, int w, R* win) {
+  const int t = threadIdx.x, nt = blockDim.x, ww = w * w;
+  for (int i0 = t; i0 < ww; i0 += 8 * nt) {
+    R v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = i0 + u * nt;
+      if (idx < ww) {
+        const int r = idx / w, c = idx - r * w;
+        v[u] = G[(int64_t)(a + r) * m + (a + c)];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = i0 + u * nt;
+      if (idx < ww) {
+        const int r = idx / w, c = idx - r * w;
+        win[r * kWinLd + c] = v[u];
+      }
+    }
+  }
+}
+
 template <typename R>
 __device__ void multi_sweep(R* G, int m, int l, int hi, int nb, R* win, R* refl, Shared& sh) {
   using Q = QrArith<R>;
@@ -465,11 +493,15 @@ __device__ void multi_sweep(R* G, int m, int l, int hi, int nb, R* win, R* refl,
     const int a = max(l, l + ts - 3 * (nb - 1) - 1);   // window rows / columns a..b
     const int b = min(hi, l + te + 3);
     const int w = b - a + 1;
-    for (int idx = t; idx < w * w; idx += nt) {
-      const int r = idx / w, c = idx - r * w;
-      win[r * kWinLd + c] = g(a + r, a + c);
-    }
+#ifdef BLM_EIG_TIMING
+    long long tq = clock64();
+#endif
+    load_window(G, m, a, w, win);
     __syncthreads();
+#ifdef BLM_EIG_TIMING
+    if (t == 0) sh.msub[0] += clock64() - tq;
+    tq = clock64();
+#endif
     {
       auto W = [&](int i, int j) -> R& { return win[(i - a) * kWinLd + (j - a)]; };
       auto clampw = [&](int i) { return min(max(i, a), b); };
@@ -562,10 +594,19 @@ __device__ void multi_sweep(R* G, int m, int l, int hi, int nb, R* win, R* refl,
       }
     }
     __syncthreads();
+#ifdef BLM_EIG_TIMING
+    if (t == 0) sh.msub[1] += clock64() - tq;
+    tq = clock64();
+#endif
     for (int idx = t; idx < w * w; idx += nt) {
       const int r = idx / w, c = idx - r * w;
       g(a + r, a + c) = win[r * kWinLd + c];
     }
+#ifdef BLM_EIG_TIMING
+    __syncthreads();
+    if (t == 0) sh.msub[2] += clock64() - tq;
+    tq = clock64();
+#endif
     // rows l..a-1 (column operations, walking right) and columns b+1..hi (row operations,
     // walking down); entry i of the run is position p0 + i, bulge j on entries 9-3j..11-3j
     const int nfa = a - l, nfb = hi - b;
@@ -611,6 +652,9 @@ __device__ void multi_sweep(R* G, int m, int l, int hi, int nb, R* win, R* refl,
       for (int i = 0; i < 3 * kNbMax; ++i) st(p0 + i, e[i]);
     }
     __syncthreads();
+#ifdef BLM_EIG_TIMING
+    if (t == 0) sh.msub[3] += clock64() - tq;
+#endif
     ts = te + 1;
   }
 }
@@ -630,6 +674,7 @@ __device__ bool hqr_windowed(R* G, int m, double* wr, double* wi, double anorm, 
   auto g = [&](int i, int j) -> R& { return G[(int64_t)i * m + j]; };
 #ifdef BLM_EIG_TIMING
   long long qt[4] = {0, 0, 0, 0}, qc = 0, nsweep = 0, nstep = 0, nmulti = 0, nsfail = 0;
+  if (t == 0) sh.msub[0] = sh.msub[1] = sh.msub[2] = sh.msub[3] = 0;
 #define QR_T0() (qc = clock64())
 #define QR_T(i) (qt[i] += clock64() - qc, qc = clock64())
 #else
@@ -760,10 +805,7 @@ __device__ bool hqr_windowed(R* G, int m, double* wr, double* wi, double anorm, 
       const int a = (ks > l) ? ks - 1 : l;         // window rows/columns a..b
       const int b = min(ke + 3, hi);
       const int w = b - a + 1;
-      for (int idx = t; idx < w * w; idx += nt) {
-        const int r = idx / w, c = idx - r * w;
-        win[r * kWinLd + c] = g(a + r, a + c);
-      }
+      load_window(G, m, a, w, win);
       __syncthreads();
       QR_T(1);
       if (t < kChase) {
@@ -886,6 +928,9 @@ __device__ bool hqr_windowed(R* G, int m, double* wr, double* wi, double anorm, 
     printf("qr m=%d sweeps %lld (multi-bulge %lld, shift failures %lld) steps %lld: deflate+shift %lld "
            "window-load %lld chase %lld far %lld cycles\n",
            m, nsweep, nmulti, nsfail, nstep, qt[0], qt[1], qt[2], qt[3]);
+  if (t == 0)
+    printf("qr m=%d multi-bulge sweeps: window loads %lld chase %lld write-back %lld outside %lld cycles\n",
+           m, sh.msub[0], sh.msub[1], sh.msub[2], sh.msub[3]);
 #endif
 #undef QR_T0
 #undef QR_T
@@ -1328,10 +1373,11 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh, Team tm
   };
   // ---- 1. scaling ----
   // (every rank needs all of dsc: each computes it into shared memory, rank 0 keeps the copy
-  // the back-transformation reads)
+  // the back-transformation reads).  S and H are read past L1 and the read-only cache: the
+  // Davidson iteration writes its projected problem in the same kernel just before the solve.
   double* dscs = dsm;
   for (int i = t; i < m; i += nt) {
-    const double s = pb.S[(int64_t)i * m + i];
+    const double s = __ldcg(pb.S + (int64_t)i * m + i);
     if (!(s > 0.0) || !isfinite(s)) ctl->flag = ST_NOT_PD;
     const double d = (s > 0.0) ? 1.0 / sqrt(s) : 0.0;
     dscs[i] = d;
@@ -1343,8 +1389,8 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh, Team tm
     const double di = dscs[i];
     for (int j = rl; j < m; j += 32) {
       const int64_t idx = (int64_t)i * m + j;
-      const double sv = pb.S[idx] * di * dscs[j];
-      const double hv = pb.H[idx] * di * dscs[j];
+      const double sv = __ldcg(pb.S + idx) * di * dscs[j];
+      const double hv = __ldcg(pb.H + idx) * di * dscs[j];
       if (!isfinite(sv) || !isfinite(hv)) ctl->flag = ST_NONFINITE;
       L[idx] = sv;
       A[idx] = hv;
@@ -1356,15 +1402,20 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh, Team tm
   // The Davidson projection's overlap is the identity (S-orthonormal basis): L = I and A = H
   // as assembled above, so the Cholesky factorisation and the reduction are skipped.
   if (!(pb.flags & kEigUnitS)) {
-    // ---- 2a. Cholesky (right-looking, lower), rank 0 ----
-    for (int k = 0; k < m && R == 0; ++k) {
+    // ---- 2a. Cholesky (right-looking, lower), rows shared out ----
+    // Step k reads column k below the diagonal and the pivot; the owners of its rows write the
+    // factor's column k into row k of the upper triangle (unused: S is symmetric and only its
+    // lower half is read) and update their trailing rows; the pivots' square roots go to hbeta
+    // (free until the Hessenberg reduction).  Nothing read in a step is written in it, so one
+    // team barrier per step suffices; the factor moves to the lower triangle at the end.
+    for (int k = 0; k < m; ++k) {
       if (t == 0) {
         const double p = L[(int64_t)k * m + k];
         if (!(p > 1e-15)) {
           sh.iscal[1] = ST_NOT_PD;
         } else {
-          L[(int64_t)k * m + k] = sqrt(p);
           sh.scal[0] = 1.0 / sqrt(p);
+          if (R == 0) hbeta[k] = sqrt(p);
         }
       }
       __syncthreads();
@@ -1372,27 +1423,34 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh, Team tm
       const double inv = sh.scal[0];
       for (int i = k + 1 + t; i < m; i += nt) {
         const double v = L[(int64_t)i * m + k] * inv;
-        L[(int64_t)i * m + k] = v;
         col[i] = v;
+        if (own_row(i)) L[(int64_t)k * m + i] = v;
       }
       __syncthreads();
+      const int i0 = k + 1 + ((gw - (k + 1)) % gnw + gnw) % gnw;   // first own row > k
       if (m <= kRows4Min) {
-        for (int i = k + 1 + rw; i < m; i += rnw)
-          row_axpy(L + (int64_t)i * m, col, col[i], k + 1, i + 1, rl);
+        for (int i = i0; i < m; i += gnw) row_axpy(L + (int64_t)i * m, col, col[i], k + 1, i + 1, rl);
       } else {
-        for (int i = k + 1 + rw; i < m; i += 4 * rnw) {
+        for (int i = i0; i < m; i += 4 * gnw) {
           double sv[4];
           int j1[4];
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
-            const int ir = i + r * rnw;
+            const int ir = i + r * gnw;
             sv[r] = ir < m ? col[ir] : 0.0;
             j1[r] = ir + 1;
           }
-          rows4_axpy(L, m, i, rnw, m, sv, j1, col, k + 1, rl);
+          rows4_axpy(L, m, i, gnw, m, sv, j1, col, k + 1, rl);
         }
       }
-      __syncthreads();
+      if (!sync()) return fail(ST_NOCONV);
+    }
+    if (sh.iscal[1] == ST_OK) {
+      // the factor into the lower triangle: row i <- column i of the upper triangle, pivot
+      for (int i = gw; i < m; i += gnw) {
+        for (int j = rl; j < i; j += 32) L[(int64_t)i * m + j] = L[(int64_t)j * m + i];
+        if (rl == 0) L[(int64_t)i * m + i] = hbeta[i];
+      }
     }
     if (R == 0 && t == 0 && sh.iscal[1] != ST_OK) ctl->flag = sh.iscal[1];
     if (!sync()) return fail(ST_NOCONV);
