@@ -37,7 +37,11 @@ def build(verbose=False, extra=()):
     srcs = sources()
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(ROOT, "include", "blm.h"))
-    if not _stale(LIB, srcs + headers + [__file__]):
+    # a library built with other extra flags (e.g. -DBLM_EIG_TIMING) is stale too
+    stamp = LIB + ".flags"
+    flags = " ".join(extra)
+    same_flags = os.path.exists(stamp) and open(stamp).read() == flags
+    if same_flags and not _stale(LIB, srcs + headers + [__file__]):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
 
@@ -59,6 +63,8 @@ def build(verbose=False, extra=()):
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
     os.replace(tmp, LIB)
+    with open(stamp, "w") as f:
+        f.write(flags)
     return LIB
 
 

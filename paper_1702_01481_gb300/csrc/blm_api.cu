@@ -1380,8 +1380,8 @@ blm_status blm_batch_create(const blm_problem* problems, int32_t count, void* st
               cudaMemcpy(b->d_blocks, blocks.data(), sizeof(EigProblem) * blocks.size(),
                          cudaMemcpyHostToDevice) == cudaSuccess;
     if (ok)
-      ok = cudaMalloc(&b->d_teamctl, eig_team_ctl_bytes((int)blocks.size() + (int)comb.size())) ==
-           cudaSuccess;
+      ok = cudaMalloc(&b->d_teamctl, eig_team_ctl_bytes((int)blocks.size()) +
+                                         eig_team_ctl_bytes((int)comb.size())) == cudaSuccess;
     if (ok && !comb.empty())
       ok = cudaMalloc((void**)&b->d_comb, sizeof(EigProblem) * comb.size()) == cudaSuccess &&
            cudaMemcpy(b->d_comb, comb.data(), sizeof(EigProblem) * comb.size(),

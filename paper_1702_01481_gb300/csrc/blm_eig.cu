@@ -20,6 +20,9 @@
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
+#include <algorithm>
+#include <memory>
+#include <vector>
 
 #include "blm_internal.cuh"
 
@@ -173,7 +176,7 @@ __device__ __forceinline__ dw dw_rcp(dw a) {
 
 // Householder reflector of house3 in double words.  (x, y, z) is first scaled by a power of two
 // near 1 / max(|x|, |y|, |z|) so that no square under- or overflows FP32.
-__device__ void house3(dw x, dw y, dw z, dw& beta, dw& v1, dw& v2, dw& alpha) {
+__device__ __forceinline__ void house3(dw x, dw y, dw z, dw& beta, dw& v1, dw& v2, dw& alpha) {
   const float amax = fmaxf(mag(x), fmaxf(mag(y), mag(z)));
   if ((mag(y) == 0.0f && mag(z) == 0.0f) || !(amax >= 1e-30f)) {   // nothing to annihilate
     beta = v1 = v2 = dw_of(0.0f);
@@ -202,7 +205,7 @@ __device__ void house3(dw x, dw y, dw z, dw& beta, dw& v1, dw& v2, dw& alpha) {
 // P (x, y, z)^T = (alpha, 0, 0)^T, alpha = -sign(x) ||(x, y, z)||.  With mu = ||(x, y, z)|| and
 // v0 = x + sign(x) mu (no cancellation), v = (v0, y, z) / v0 and beta = 2 v0^2 / (v0^2 + y^2 + z^2)
 // = 1 + |x| / mu, so one reciprocal square root and one reciprocal suffice.
-__device__ void house3(double x, double y, double z, double& beta, double& v1, double& v2,
+__device__ __forceinline__ void house3(double x, double y, double z, double& beta, double& v1, double& v2,
                        double& alpha) {
   const double sigma = fma(z, z, y * y);
   if (sigma == 0.0) {
@@ -237,6 +240,8 @@ struct Shared {
   int out_pos[kMaxKeep];    // output position of each selection entry (ascending eigenvalues)
 #ifdef BLM_EIG_TIMING
   long long msub[4];        // multi-bulge sweeps: window loads, chase, write-back, outside
+  long long mphase[3];      // the chase's phases 0 (reflectors), 1 (rows), 2 (columns)
+  long long msteps;         // the chase's time steps
 #endif
 };
 
@@ -250,7 +255,7 @@ struct Shared {
 // ---------------------------------------------------------------------------------------------
 constexpr int kNbMax = 4;       // bulges chased together
 
-__device__ void house3f(float x, float y, float z, float& beta, float& v1, float& v2,
+__device__ __forceinline__ void house3f(float x, float y, float z, float& beta, float& v1, float& v2,
                         float& alpha) {
   const float sigma = fmaf(z, z, y * y);
   if (sigma == 0.0f) {
@@ -259,12 +264,18 @@ __device__ void house3f(float x, float y, float z, float& beta, float& v1, float
     alpha = x;
     return;
   }
-  const float mu = sqrtf(fmaf(x, x, sigma));
+  // (the FP32 QR only locates eigenvalues, which FP64 inverse iteration recomputes: the
+  // hardware reciprocal square root and approximate division, a few units in the last place,
+  // keep this step's latency short)
+  const float n2 = fmaf(x, x, sigma);
+  const float rmu = rsqrtf(n2);
+  const float mu = n2 * rmu;
   const float sg = x < 0.0f ? -1.0f : 1.0f;
   const float v0 = fmaf(sg, mu, x);
-  v1 = y / v0;
-  v2 = z / v0;
-  beta = 1.0f + fabsf(x) / mu;
+  const float rv0 = __fdividef(1.0f, v0);
+  v1 = y * rv0;
+  v2 = z * rv0;
+  beta = fmaf(fabsf(x), rmu, 1.0f);
   alpha = -sg * mu;
 }
 
@@ -455,14 +466,14 @@ struct QrArith<dw> {
 // Rows above and columns right of the window receive the same operations afterwards from the
 // stored reflectors, all bulges of one time step on a sliding run of 3 kNbMax entries (their
 // ranges are disjoint and adjacent), time steps in order.
-// The w x w window at (a, a) of G into shared memory, eight loads in flight per thread.
+// The w x w window at (a, a) of G into shared memory, four loads in flight per thread.
 template <typename R>
 __device__ __forceinline__ void load_window(const R* G, int m, int a, int w, R* win) {
   const int t = threadIdx.x, nt = blockDim.x, ww = w * w;
-  for (int i0 = t; i0 < ww; i0 += 8 * nt) {
-    R v[8];
+  for (int i0 = t; i0 < ww; i0 += 2 * nt) {
+    R v[2];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < 2; ++u) {
       const int idx = i0 + u * nt;
       if (idx < ww) {
         const int r = idx / w, c = idx - r * w;
@@ -470,7 +481,7 @@ __device__ __forceinline__ void load_window(const R* G, int m, int a, int w, R* 
       }
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < 2; ++u) {
       const int idx = i0 + u * nt;
       if (idx < ww) {
         const int r = idx / w, c = idx - r * w;
@@ -510,6 +521,10 @@ __device__ void multi_sweep(R* G, int m, int l, int hi, int nb, R* win, R* refl,
       const int js = t / kWin, tl = t - js * kWin;
       for (int tau = ts; tau <= te; ++tau) {
         R* rft = refl + (tau - ts) * kNbMax * 4;   // (beta, v1, v2, alpha) of each slot
+#ifdef BLM_EIG_TIMING
+        long long tp = clock64();
+        if (t == 0) ++sh.msteps;
+#endif
         if (t < kChase) {
           // phase 0: warp j forms slot j's reflector from its bulge column (or, at k = l, from
           // the shift polynomial's first column)
@@ -542,6 +557,10 @@ __device__ void multi_sweep(R* G, int m, int l, int hi, int nb, R* win, R* refl,
           }
         }
         __syncthreads();
+#ifdef BLM_EIG_TIMING
+        if (t == 0) sh.mphase[0] += clock64() - tp;
+        tp = clock64();
+#endif
         const int k = l + tau - 3 * js;
         const R be = rft[4 * js], v1 = rft[4 * js + 1], v2 = rft[4 * js + 2], al = rft[4 * js + 3];
         const bool act = js < nb && k >= l && k <= hi - 1 && mag(be) != 0;
@@ -559,6 +578,10 @@ __device__ void multi_sweep(R* G, int m, int l, int hi, int nb, R* win, R* refl,
           }
         }
         __syncthreads();
+#ifdef BLM_EIG_TIMING
+        if (t == 0) sh.mphase[1] += clock64() - tp;
+        tp = clock64();
+#endif
         // phase 2: slot js's bulge column and column operations on row r.  Column k + 2 is the
         // leading slot's (js - 1) annihilated bulge column: on its row k + 3 that slot's alpha
         // enters this operation, and this slot's result is what the entry keeps (the leading
@@ -591,6 +614,9 @@ __device__ void multi_sweep(R* G, int m, int l, int hi, int nb, R* win, R* refl,
           }
         }
         __syncthreads();
+#ifdef BLM_EIG_TIMING
+        if (t == 0) sh.mphase[2] += clock64() - tp;
+#endif
       }
     }
     __syncthreads();
@@ -674,7 +700,10 @@ __device__ bool hqr_windowed(R* G, int m, double* wr, double* wi, double anorm, 
   auto g = [&](int i, int j) -> R& { return G[(int64_t)i * m + j]; };
 #ifdef BLM_EIG_TIMING
   long long qt[4] = {0, 0, 0, 0}, qc = 0, nsweep = 0, nstep = 0, nmulti = 0, nsfail = 0;
-  if (t == 0) sh.msub[0] = sh.msub[1] = sh.msub[2] = sh.msub[3] = 0;
+  if (t == 0) {
+    sh.msub[0] = sh.msub[1] = sh.msub[2] = sh.msub[3] = 0;
+    sh.mphase[0] = sh.mphase[1] = sh.mphase[2] = sh.msteps = 0;
+  }
 #define QR_T0() (qc = clock64())
 #define QR_T(i) (qt[i] += clock64() - qc, qc = clock64())
 #else
@@ -929,8 +958,10 @@ __device__ bool hqr_windowed(R* G, int m, double* wr, double* wi, double anorm, 
            "window-load %lld chase %lld far %lld cycles\n",
            m, nsweep, nmulti, nsfail, nstep, qt[0], qt[1], qt[2], qt[3]);
   if (t == 0)
-    printf("qr m=%d multi-bulge sweeps: window loads %lld chase %lld write-back %lld outside %lld cycles\n",
-           m, sh.msub[0], sh.msub[1], sh.msub[2], sh.msub[3]);
+    printf("qr m=%d multi-bulge sweeps: window loads %lld chase %lld write-back %lld outside %lld cycles; "
+           "%lld time steps: reflectors %lld rows %lld columns %lld cycles\n",
+           m, sh.msub[0], sh.msub[1], sh.msub[2], sh.msub[3], sh.msteps, sh.mphase[0], sh.mphase[1],
+           sh.mphase[2]);
 #endif
 #undef QR_T0
 #undef QR_T
@@ -2053,21 +2084,53 @@ eig_kernel(const EigProblem* __restrict__ probs) {
 }
 
 // CTA c of a team launch solves problem prob[c] as rank rank[c] of size[c] CTAs.
+// A team launch: CTA c < nteam solves problem prob[c] as rank rank[c] of size[c] CTAs; then
+// every CTA takes the problems of the queue (largest first) one at a time from a shared counter.
 constexpr int kTeamGridMax = 160;
+constexpr int kQueueMax = 4096;
 struct TeamMap {
   uint16_t prob[kTeamGridMax];
   uint8_t rank[kTeamGridMax];
   uint8_t size[kTeamGridMax];
+  int nteam, nqueue;
+  uint16_t queue[kQueueMax];
 };
 
-__global__ void __launch_bounds__(kEigThreads)
-eig_team_kernel(const EigProblem* __restrict__ probs, TeamCtl* ctl, const __grid_constant__ TeamMap map) {
+template <bool kQueue>
+__global__ void __launch_bounds__(kEigThreads, 1)
+eig_team_kernel(const EigProblem* __restrict__ probs, TeamCtl* ctl, int* queue_head,
+                const __grid_constant__ TeamMap map) {
   extern __shared__ double dsm[];
   __shared__ Shared sh;
-  const int p = map.prob[blockIdx.x];
-  const EigProblem pb = probs[p];
-  if (pb.run_if_noconv && *pb.run_if_noconv != ST_NOCONV) return;
-  dense_geig(pb, dsm, sh, Team{(int)map.rank[blockIdx.x], (int)map.size[blockIdx.x], ctl + p});
+  if constexpr (!kQueue) {
+    // one task per CTA (fewer problems than SMs)
+    const int p = map.prob[blockIdx.x];
+    const EigProblem pb = probs[p];
+    if (pb.run_if_noconv && *pb.run_if_noconv != ST_NOCONV) return;
+    dense_geig(pb, dsm, sh, Team{(int)map.rank[blockIdx.x], (int)map.size[blockIdx.x], ctl + p});
+  } else {
+  __shared__ int qi;
+  bool first = true;
+  for (;;) {
+    // (one call site of the solver, so that it is inlined)
+    int p;
+    Team tm{0, 1, nullptr};
+    if (first && (int)blockIdx.x < map.nteam) {
+      p = map.prob[blockIdx.x];
+      tm = Team{(int)map.rank[blockIdx.x], (int)map.size[blockIdx.x], ctl + p};
+    } else {
+      __syncthreads();   // (every thread is done with the previous problem and with qi)
+      if (threadIdx.x == 0) qi = map.nqueue > 0 ? atomicAdd(queue_head, 1) : map.nqueue;
+      __syncthreads();
+      if (qi >= map.nqueue) break;
+      p = map.queue[qi];
+    }
+    first = false;
+    const EigProblem pb = probs[p];
+    if (pb.run_if_noconv && *pb.run_if_noconv != ST_NOCONV) continue;
+    dense_geig(pb, dsm, sh, tm);
+  }
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -2455,9 +2518,13 @@ cudaError_t launch_davidson(const EigProblem* probs, double tol, int max_iter, d
   return cudaLaunchKernelEx(&cfg, davidson_kernel, probs, tol, max_iter, ctl);
 }
 
-size_t eig_team_ctl_bytes(int nprob) { return sizeof(TeamCtl) * (size_t)(nprob > 0 ? nprob : 0); }
+// per problem a team control block, then the queue counter
+size_t eig_team_ctl_bytes(int nprob) {
+  return sizeof(TeamCtl) * (size_t)(nprob > 0 ? nprob : 0) + 256;
+}
 
-// CTAs per problem.  The estimated time of a problem of dimension d on T CTAs is
+// CTAs per problem (launches with fewer problems than SMs).  The estimated time of a problem of
+// dimension d on T CTAs is
 // d^3 (5 / T + 1): the FP64 reductions and eigenvectors (about 5 d^3 cycles on one CTA) are
 // shared out, the QR (about d^3 with the FP32 location) is not.  Starting from one CTA each,
 // the slowest problems get one more CTA together while the SMs last.
@@ -2488,29 +2555,69 @@ void launch_eig(const EigProblem* probs, int nprob, int threads, cudaStream_t st
   static int sms = 0;
   if (sms == 0) {
     cudaFuncSetAttribute(eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(eig_team_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(eig_team_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(eig_team_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int dev = 0, n = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eig_team_kernel, kEigThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eig_team_kernel<true>, kEigThreads, smem);
     sms = std::min(n * std::max(per_sm, 1), kTeamGridMax);
   }
-  std::vector<int> T;
-  if (dims != nullptr && team_ctl != nullptr && nprob < sms) T = team_sizes(dims, nprob, sms);
-  int grid = 0;
-  for (int v : T) grid += v;
-  if (grid <= nprob) {
+  if (dims == nullptr || team_ctl == nullptr || nprob > kQueueMax) {
     eig_kernel<<<nprob, kEigThreads, smem, st>>>(probs);
     return;
   }
-  TeamMap map = {};
-  for (int p = 0, c = 0; p < nprob; ++p)
-    for (int r = 0; r < T[p]; ++r, ++c) {
-      map.prob[c] = (uint16_t)p;
-      map.rank[c] = (uint8_t)r;
-      map.size[c] = (uint8_t)T[p];
+  auto est = [&](int p, int T) { const double d = dims[p]; return d * d * d * (5.0 / T + 1.0); };
+  std::unique_ptr<TeamMap> mp(new TeamMap());   // (the launch parameter, staged on the host)
+  TeamMap& map = *mp;
+  int grid = 0;
+  if (nprob < sms) {
+    // every problem on its own CTAs
+    const std::vector<int> T = team_sizes(dims, nprob, sms);
+    for (int p = 0; p < nprob; ++p)
+      for (int r = 0; r < T[p]; ++r, ++grid) {
+        map.prob[grid] = (uint16_t)p;
+        map.rank[grid] = (uint8_t)r;
+        map.size[grid] = (uint8_t)T[p];
+      }
+    if (grid <= nprob) {
+      eig_kernel<<<nprob, kEigThreads, smem, st>>>(probs);
+      return;
     }
+    map.nteam = grid;
+  } else {
+    // more problems than SMs: the ones slower than the balanced share of all the work get
+    // teams (the smallest that bring them within it, at most kMaxTeam, half the SMs at most);
+    // every CTA then works through the rest, largest first
+    double total = 0.0;
+    for (int p = 0; p < nprob; ++p) total += est(p, 1);
+    const double share = total / sms;
+    std::vector<int> order(nprob);
+    for (int p = 0; p < nprob; ++p) order[p] = p;
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return est(a, 1) > est(b, 1); });
+    int c = 0;
+    for (int p : order) {
+      if (est(p, 1) <= share || dims[p] <= kRows4Min) {
+        map.queue[map.nqueue++] = (uint16_t)p;
+        continue;
+      }
+      int T = 2;
+      while (T < kMaxTeam && est(p, T) > share) ++T;
+      if (c + T > sms / 2) {
+        map.queue[map.nqueue++] = (uint16_t)p;
+        continue;
+      }
+      for (int r = 0; r < T; ++r, ++c) {
+        map.prob[c] = (uint16_t)p;
+        map.rank[c] = (uint8_t)r;
+        map.size[c] = (uint8_t)T;
+      }
+    }
+    map.nteam = c;
+    grid = sms;
+  }
   if (cudaMemsetAsync(team_ctl, 0, eig_team_ctl_bytes(nprob), st) != cudaSuccess) return;
+  int* queue_head = reinterpret_cast<int*>(static_cast<char*>(team_ctl) + sizeof(TeamCtl) * (size_t)nprob);
   // a cooperative launch (every CTA resident: the team barriers need it), in the
   // launch-attribute form that stream capture accepts
   cudaLaunchConfig_t cfg = {};
@@ -2523,7 +2630,12 @@ void launch_eig(const EigProblem* probs, int nprob, int threads, cudaStream_t st
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, eig_team_kernel, probs, reinterpret_cast<TeamCtl*>(team_ctl), map);
+  if (map.nqueue > 0)
+    cudaLaunchKernelEx(&cfg, eig_team_kernel<true>, probs, reinterpret_cast<TeamCtl*>(team_ctl),
+                       queue_head, map);
+  else
+    cudaLaunchKernelEx(&cfg, eig_team_kernel<false>, probs, reinterpret_cast<TeamCtl*>(team_ctl),
+                       queue_head, map);
 }
 
 }  // namespace blm
