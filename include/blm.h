@@ -258,7 +258,7 @@ const char* blm_profile_class_name(int i);
  * (device, n_keep) and the corresponding directions into B (device, n_keep x (dim - 1),
  * unit 2-norm, largest-magnitude entry positive), exactly as blm_get_block reports them.
  *
- * Workspace: a static device array inside the library (about 11.6 MB, held by every GPU that
+ * Workspace: a static device array inside the library (about 20.3 MB, held by every GPU that
  * loads the library until the process exits); nothing is allocated or freed.  Limits: 2 <= dim
  * <= blm_noalloc_max_dim() (257), 1 <= n_keep <= min(64, dim - 1); larger sizes return
  * BLM_ERR_ARG with a message on stderr.  The first call on each device looks up the array's

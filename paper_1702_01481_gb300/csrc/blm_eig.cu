@@ -974,7 +974,8 @@ __device__ bool hqr_windowed(R* G, int m, double* wr, double* wi, double anorm, 
 // with the factors.  Rows being eliminated live in shared memory (cur, nxt); U is stored packed
 // (row k holds columns k..m-1).  CX selects complex arithmetic (complex shift) at compile time.
 // ---------------------------------------------------------------------------------------------
-constexpr int kVecWarps = 16;                          // warps running inverse iteration
+constexpr int kVecWarps = 16;                          // warps of a CTA running inverse iteration
+constexpr int kVecSlots = 32;                          // factor slots of a problem (its team's warps)
 constexpr int kEigSmemDoubles = 200 * 1024 / 8;        // dynamic shared memory of the solver
 static_assert(kQrSmemDoubles <= kEigSmemDoubles, "QR window exceeds the solver's shared memory");
 
@@ -982,12 +983,12 @@ static_assert(kQrSmemDoubles <= kEigSmemDoubles, "QR window exceeds the solver's
 // then the per-warp factors and pivots and the kMaxKeep Hessenberg-basis eigenvectors.
 __host__ __device__ constexpr int64_t eig_base_doubles(int64_t m) { return 5 * m * m + 6 * m; }
 constexpr int kMaxTeam = 8;                             // CTAs per problem at most
-// ranks 1.. of a team keep their two scratch vectors after the eigenvector section
+// the end of the eigenvector section
 __host__ __device__ constexpr int64_t eig_rank_offset(int64_t m) {
-  return eig_base_doubles(m) + kVecWarps * m * (m + 1) + kVecWarps * 3 * m + kMaxKeep * 2 * m;
+  return eig_base_doubles(m) + kVecSlots * m * (m + 1) + kVecSlots * 3 * m + kMaxKeep * 2 * m;
 }
 __host__ __device__ constexpr int64_t eig_total_doubles(int64_t m) {
-  return eig_rank_offset(m) + (int64_t)(kMaxTeam - 1) * 2 * m + 64;
+  return eig_rank_offset(m) + 64;
 }
 
 __device__ __forceinline__ int64_t urow(int k, int m) {
@@ -1370,14 +1371,15 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh, Team tm
   double* hbeta = dsc + m;
   double* wr = hbeta + m;
   double* wi = wr + m;
-  // per-rank vectors (m each): rank 0 in the base area, the others after the last section
-  double* col = tm.r == 0 ? wi + m : pb.work + eig_rank_offset(m) + (int64_t)(tm.r - 1) * 2 * m;
+  // each rank's two work vectors (m each) at the end of its shared memory (the left update's
+  // partial sums fill the rest of it; the QR windows and the eigenvector buffers reuse it later)
+  double* col = dsm + kEigSmemDoubles - 2 * (int64_t)m;
   double* vtmp = col + m;
   // per-warp inverse iteration: packed U, pivots; then the Hessenberg-basis eigenvectors
-  double* Uw = pb.work + eig_base_doubles(m);                 // kVecWarps x m (m + 1)
-  double* plw = Uw + (int64_t)kVecWarps * m * (m + 1);        // kVecWarps x 2m
-  int* psw = reinterpret_cast<int*>(plw + (int64_t)kVecWarps * 2 * m);   // kVecWarps x m ints
-  double* cvec = plw + (int64_t)kVecWarps * 3 * m;            // kMaxKeep x 2m
+  double* Uw = pb.work + eig_base_doubles(m);                 // kVecSlots x m (m + 1)
+  double* plw = Uw + (int64_t)kVecSlots * m * (m + 1);        // kVecSlots x 2m
+  int* psw = reinterpret_cast<int*>(plw + (int64_t)kVecSlots * 2 * m);   // kVecSlots x m ints
+  double* cvec = plw + (int64_t)kVecSlots * 3 * m;            // kMaxKeep x 2m
 
 #ifdef BLM_EIG_TIMING
   long long tmark[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -1395,7 +1397,12 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh, Team tm
   }
   __syncthreads();
   const int rw = t >> 5, rl = t & 31, rnw = nt >> 5;
-  const int gw = R * rnw + rw, gnw = T * rnw;   // this warp among the team's warps
+  const int gw = R * rnw + rw, gnw = T * rnw;
+  // shared memory: the per-warp inverse-iteration buffers (6 m) bound the dimension
+  if (6 * (int64_t)m > kEigSmemDoubles) {
+    if (t == 0) *pb.status = ST_NOCONV;
+    return;
+  }   // this warp among the team's warps
   auto own_row = [&](int i) { return (i % gnw) / rnw == R; };
   // the team's status word: any rank may set it; read after a barrier
   auto flag = [&]() { return *(volatile int*)&ctl->flag; };
@@ -1582,30 +1589,35 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh, Team tm
       // left: rows k+1.., this rank's columns k..: w = beta u^T A from per-warp partial sums
       // over rows (each warp a slice of the rows, lanes over columns: coalesced, loads
       // independent), then A -= u w
-      double* wpart = dsm;                          // rnw x m (shared memory is free here)
-      for (int p = first_piece(k, R, T); 32 * p < m; p += T) {
-        const int j = 32 * p + rl;
-        if (j >= k && j < m) {
-          const double* __restrict__ aj = A + j;
-          const double* __restrict__ u = col;
-          double acc0 = 0.0, acc1 = 0.0;
-          int i = k + 1 + rw;
-          for (; i + rnw < m; i += 2 * rnw) {
-            acc0 = fma(u[i], aj[(int64_t)i * m], acc0);
-            acc1 = fma(u[i + rnw], aj[(int64_t)(i + rnw) * m], acc1);
+      // (in chunks of columns that fit the shared memory before col and vtmp)
+      double* wpart = dsm;                          // rnw x chunk
+      const int chunk = max(32, (int)((kEigSmemDoubles - 2 * (int64_t)m) / rnw) / 32 * 32);
+      for (int jb = (k >> 5) << 5; jb < m; jb += chunk) {
+        const int je = min(m, jb + chunk);
+        for (int p = first_piece(max(k, jb), R, T); 32 * p < je; p += T) {
+          const int j = 32 * p + rl;
+          if (j >= k && j < je) {
+            const double* __restrict__ aj = A + j;
+            const double* __restrict__ u = col;
+            double acc0 = 0.0, acc1 = 0.0;
+            int i = k + 1 + rw;
+            for (; i + rnw < m; i += 2 * rnw) {
+              acc0 = fma(u[i], aj[(int64_t)i * m], acc0);
+              acc1 = fma(u[i + rnw], aj[(int64_t)(i + rnw) * m], acc1);
+            }
+            if (i < m) acc0 = fma(u[i], aj[(int64_t)i * m], acc0);
+            wpart[rw * chunk + (j - jb)] = acc0 + acc1;
           }
-          if (i < m) acc0 = fma(u[i], aj[(int64_t)i * m], acc0);
-          wpart[rw * m + j] = acc0 + acc1;
         }
+        __syncthreads();
+        for (int j = max(k, jb) + t; j < je; j += nt) {
+          if (!own_col(j)) continue;
+          double sum = 0.0;
+          for (int w2 = 0; w2 < rnw; ++w2) sum += wpart[w2 * chunk + (j - jb)];
+          vtmp[j] = beta * sum;
+        }
+        __syncthreads();
       }
-      __syncthreads();
-      for (int j = k + t; j < m; j += nt) {
-        if (!own_col(j)) continue;
-        double sum = 0.0;
-        for (int w2 = 0; w2 < rnw; ++w2) sum += wpart[w2 * m + j];
-        vtmp[j] = beta * sum;
-      }
-      __syncthreads();
       if (m <= kRows4Min) {
         for (int i = k + 1 + rw; i < m; i += rnw)
           row_axpy_own(A + (int64_t)i * m, vtmp, col[i], k, m, rl, R, T);
@@ -1801,8 +1813,8 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh, Team tm
     // ---- 5. eigenvectors of the Hessenberg matrix: inverse iteration, one warp per job ----
     // The shift is the located eigenvalue, so three solves from a fixed start vector converge;
     // the residual ||Hh y - lambda y|| is checked before the vector is used.
-    // (the team's vector warps share the kVecWarps factor slots: global vector warp gv)
-    const int nvw = min(max(1, kVecWarps / T), (int)((kEigSmemDoubles) / (6 * (int64_t)m)));
+    // (the team's vector warps share the kVecSlots factor slots: global vector warp gv)
+    const int nvw = min(min(kVecWarps, max(1, kVecSlots / T)), (int)((kEigSmemDoubles) / (6 * (int64_t)m)));
     const int gv = R * nvw + warp, gnv = T * nvw;
     if (warp < nvw) {
       double* cur = dsm + (int64_t)warp * 6 * m;
