@@ -1383,6 +1383,12 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh, Team tm
 
 #ifdef BLM_EIG_TIMING
   long long tmark[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long hsub[6] = {0, 0, 0, 0, 0, 0}, hc = 0;   // Hessenberg: reflector, left, barrier, right, barrier
+#define HS_T0() (hc = clock64())
+#define HS_T(i) (hsub[i] += clock64() - hc, hc = clock64())
+#else
+#define HS_T0() ((void)0)
+#define HS_T(i) ((void)0)
 #endif
   EIG_MARK(0);
   if (t == 0) {
@@ -1560,6 +1566,7 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh, Team tm
   // over rows) is shared out by column pieces, the right update (a reduction over columns) by
   // rows, with a team barrier after each.
   for (int k = 0; k < m - 2; ++k) {
+    HS_T0();
     double part = 0.0;
     for (int i = k + 2 + t; i < m; i += nt) {
       const double v = A[(int64_t)i * m + k];
@@ -1585,6 +1592,7 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh, Team tm
     const double rv0 = rcp_nr(v0);
     for (int i = k + 1 + t; i < m; i += nt) col[i] = (i == k + 1) ? 1.0 : A[(int64_t)i * m + k] * rv0;
     __syncthreads();
+    HS_T(0);
     if (beta != 0.0) {
       // left: rows k+1.., this rank's columns k..: w = beta u^T A from per-warp partial sums
       // over rows (each warp a slice of the rows, lanes over columns: coalesced, loads
@@ -1599,14 +1607,16 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh, Team tm
           if (j >= k && j < je) {
             const double* __restrict__ aj = A + j;
             const double* __restrict__ u = col;
-            double acc0 = 0.0, acc1 = 0.0;
+            double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
             int i = k + 1 + rw;
-            for (; i + rnw < m; i += 2 * rnw) {
+            for (; i + 3 * rnw < m; i += 4 * rnw) {   // four independent loads in flight
               acc0 = fma(u[i], aj[(int64_t)i * m], acc0);
               acc1 = fma(u[i + rnw], aj[(int64_t)(i + rnw) * m], acc1);
+              acc2 = fma(u[i + 2 * rnw], aj[(int64_t)(i + 2 * rnw) * m], acc2);
+              acc3 = fma(u[i + 3 * rnw], aj[(int64_t)(i + 3 * rnw) * m], acc3);
             }
-            if (i < m) acc0 = fma(u[i], aj[(int64_t)i * m], acc0);
-            wpart[rw * chunk + (j - jb)] = acc0 + acc1;
+            for (; i < m; i += rnw) acc0 = fma(u[i], aj[(int64_t)i * m], acc0);
+            wpart[rw * chunk + (j - jb)] = (acc0 + acc1) + (acc2 + acc3);
           }
         }
         __syncthreads();
@@ -1634,7 +1644,12 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh, Team tm
           rows4_axpy_own(A, m, i, rnw, m, sv, j1, vtmp, k, rl, R, T);
         }
       }
+#ifdef BLM_EIG_TIMING
+      __syncthreads();
+#endif
+      HS_T(1);
       if (!sync()) return fail(ST_NOCONV);
+      HS_T(2);
       // right: this rank's rows, columns k+1..
       if (m <= kRows4Min) {
         for (int i = gw; i < m; i += gnw) {
@@ -1645,11 +1660,16 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh, Team tm
       } else {
         for (int i = gw; i < m; i += 4 * gnw) rows4_dot_axpy(A, m, i, gnw, m, col, beta, k + 1, m, rl);
       }
+#ifdef BLM_EIG_TIMING
+      __syncthreads();
+#endif
+      HS_T(3);
     }
     // store the reflector below the subdiagonal (the rank that updated column k)
     if (own_col(k))
       for (int i = k + 2 + t; i < m; i += nt) A[(int64_t)i * m + k] = col[i];
     if (!sync()) return fail(ST_NOCONV);
+    HS_T(4);
   }
   // ---- Hessenberg copies: Hh (inverse iteration) and the QR working copy in W ----
   double amx = 0.0;
@@ -2080,9 +2100,10 @@ __device__ void dense_geig(const EigProblem pb, double* dsm, Shared& sh, Team tm
   EIG_MARK(6);
 #ifdef BLM_EIG_TIMING
   if (t == 0 && R == 0 && blockIdx.x == 0)
-    printf("eig timing m=%d: scale %lld chol+std %lld hess %lld qr %lld vec %lld back %lld cycles\n",
+    printf("eig timing m=%d: scale %lld chol+std %lld hess %lld qr %lld vec %lld back %lld cycles; "
+           "hessenberg: reflector %lld left %lld barrier %lld right %lld store+barrier %lld\n",
            m, tmark[1] - tmark[0], tmark[2] - tmark[1], tmark[3] - tmark[2], tmark[4] - tmark[3],
-           tmark[5] - tmark[4], tmark[6] - tmark[5]);
+           tmark[5] - tmark[4], tmark[6] - tmark[5], hsub[0], hsub[1], hsub[2], hsub[3], hsub[4]);
 #endif
 }
 
