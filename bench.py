@@ -528,7 +528,8 @@ def run_batch(args):
         ach = fl / (kms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 3), "unit": "TFLOP/s",
                 "frac": round(ach / peak, 4), "traffic": None,
-                "kernel": "eig_kernel (FP64 block solves; summed over the problems' eager steps)",
+                "kernel": "eig_team_kernel (block solves of all problems in one persistent launch; "
+                          "summed over the problems' eager steps)",
                 "per_launch_algorithmic_flop": fl}
     else:
         roof = {"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
