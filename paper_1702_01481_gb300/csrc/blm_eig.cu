@@ -2173,7 +2173,7 @@ eig_team_kernel(const EigProblem* __restrict__ probs, TeamCtl* ctl, int* queue_h
 // dense routine above); the Ritz pair with the lowest real part is expanded with the diagonal
 // preconditioner t = -(diag H - theta diag S)^-1 r, starting from the Psi direction e_0.
 // Converged when ||H u - theta S u|| <= tol * ||S u|| * max(1, |theta|), or when that ratio has
-// stayed within 100 tol for six iterations without halving (the rounding floor).
+// stayed within 10 tol for ten iterations without halving (the rounding floor).
 // ---------------------------------------------------------------------------------------------
 constexpr int kDavMax = 40;
 
@@ -2422,7 +2422,7 @@ davidson_kernel(const EigProblem* __restrict__ probs, double tol, int max_iter, 
     const double sn = sqrt(dotv(Su, Su, m, sh));
     DAV_T(2);
     // Converged at tol; or, where rounding keeps the residual from reaching tol (its floor is
-    // about m eps ||H|| ||u||), once it has stayed within 100 tol for six iterations without
+    // about m eps ||H|| ||u||), once it has stayed within 10 tol for ten iterations without
     // halving.
     const double rel = rn / (sn * fmax(1.0, fabs(theta)));
     if (rel < 0.5 * best_rel) {
@@ -2431,7 +2431,7 @@ davidson_kernel(const EigProblem* __restrict__ probs, double tol, int max_iter, 
     } else {
       ++since_best;
     }
-    if (rel <= tol || (best_rel <= 100.0 * tol && since_best >= 6)) {
+    if (rel <= tol || (best_rel <= 10.0 * tol && since_best >= 10)) {
       status = ST_OK;
       break;
     }

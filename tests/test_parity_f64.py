@@ -212,3 +212,15 @@ def test_blocks_of_256_windowed_qr(torch_cuda):
     ref = blm_oracle.blm_step(O, G, E, None, wl.block_offsets, wl.n_keep)
     got = run_gpu(torch_cuda, O, G, E, None, wl.block_offsets, wl.n_keep)
     compare(got, ref, O, G, E, None, wl.block_offsets, wl.n_keep)
+
+
+def test_more_block_problems_than_sms(torch_cuda):
+    """170 block problems (more than the GPU's 152 SMs): the block solves run as one persistent
+    grid, the three 200-parameter blocks on teams of CTAs and the 167 blocks of 8 taken one at a
+    time from the shared queue; the combined problem (dimension 681) goes to Davidson."""
+    offs = [0, 200, 400, 600] + [600 + 8 * (i + 1) for i in range(167)]
+    wl = synth.Workload("t", offs[-1], 3000, offs, 4, decades=4.0, chunk=3000, seed=21)
+    O, G, E = synth.samples(wl)
+    ref = blm_oracle.blm_step(O, G, E, None, wl.block_offsets, wl.n_keep)
+    got = run_gpu(torch_cuda, O, G, E, None, wl.block_offsets, wl.n_keep)
+    compare(got, ref, O, G, E, None, wl.block_offsets, wl.n_keep)
