@@ -158,8 +158,9 @@ blm_status blm_graph_result(blm_handle* h, double* e_pred);
  * step of every problem, from the device arrays O[i], dEL[i], EL[i], w[i] (w or its entries may
  * be NULL) of n_samples[i] rows with stride ld[i], taken in chunks of `chunk` samples, with
  * Delta mu written to the device array dmu[i]: the problems' sweeps run on parallel branches of
- * the graph, the block eigen-solves of all problems in one launch (one CTA per block problem
- * across the whole batch), the dense combined solves of all problems in one launch, larger
+ * the graph, the block eigen-solves of all problems in one launch (the largest block problems
+ * on teams of CTAs, the rest taken one CTA at a time from a shared queue), the dense combined
+ * solves of all problems in one launch, larger
  * combined problems by Davidson one after another.  blm_batch_launch enqueues the graph on
  * `stream`; blm_batch_result synchronises it and writes every problem's predicted energy
  * (NaN where it failed) and, if status is not NULL, its blm_status; it returns BLM_OK if every
